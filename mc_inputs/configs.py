@@ -1,0 +1,169 @@
+"""The five synthetic workloads, each a seeded recipe.
+
+Every workload lives on the unit square with nx = ny = n square cells of side
+h = 1/n. Continua are ordered by ascending permeability (the ordering the L-
+and U-schemes of Section 3.3 assume). Sources are cell-integrated rates F
+(Eq. app-mc: F = f |cell|), given directly: +1 in cell (n/8, n/8) and -1 in
+cell (7n/8, 7n/8) of the most permeable continuum.
+
+Exchange coefficients are given per unit area (sigma of Eq. mm); a constant
+L x L matrix `sigma` and, for cells where the exchange varies, per-pair arrays
+`sigma_cell[(a, b)]` (a < b) that replace the constant for that pair.
+"""
+
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+
+from .fields import correlated_lognormal, random_segments, segment_lengths
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    L: int
+    k: List[np.ndarray]                     # L arrays (ny, nx)
+    c: np.ndarray                           # (L,)
+    sigma: np.ndarray                       # (L, L) symmetric, zero diagonal
+    tau: float
+    nsteps: int
+    F: List[np.ndarray]                     # L arrays (ny, nx)
+    p0: List[np.ndarray]                    # L arrays (ny, nx)
+    sigma_cell: Dict[Tuple[int, int], np.ndarray] = field(default_factory=dict)
+    coarse: Optional[Tuple[int, int, int]] = None   # (ncx, ncy, layers)
+    seed: Optional[int] = None
+
+    @property
+    def h(self):
+        return 1.0 / self.nx
+
+    @property
+    def cells(self):
+        return self.nx * self.ny
+
+    @property
+    def continuum_cells(self):
+        return self.L * self.nx * self.ny
+
+
+def _sym(L, pairs):
+    s = np.zeros((L, L))
+    for (a, b), v in pairs.items():
+        s[a, b] = s[b, a] = v
+    return s
+
+
+def _point_sources(n, L, alpha):
+    F = [np.zeros((n, n)) for _ in range(L)]
+    a, b = n // 8, (7 * n) // 8
+    F[alpha][a, a] += 1.0
+    F[alpha][b, b] -= 1.0
+    return F
+
+
+def dual_64(n=64, seed=1):
+    """Dual-continuum matrix/fracture problem: k1 = exp(N(0,1)) per cell,
+    k2 = 1e3 exp(0.5 N(0,1)) (drawn in that order from one generator),
+    c = (1, 0.1), sigma_12 = 10, tau = 1/50, 50 steps from p = 0."""
+    rng = np.random.default_rng(seed)
+    k1 = np.exp(rng.standard_normal((n, n)))
+    k2 = 1e3 * np.exp(0.5 * rng.standard_normal((n, n)))
+    return Workload("dual_%d" % n, n, n, 2, [k1, k2], np.array([1.0, 0.1]),
+                    _sym(2, {(0, 1): 10.0}), 1.0 / 50, 50,
+                    _point_sources(n, 2, 1), [np.zeros((n, n))] * 2, seed=seed)
+
+
+def triple_1024(n=1024, seeds=(21, 22, 23), nsteps=200):
+    """Three continua with correlated log-normal k (correlation length 16
+    cells, geometric means 1, 1e2, 1e4), c = (1, 0.2, 0.05),
+    sigma = (12: 5, 13: 1, 23: 20), tau = 1/200."""
+    k = [correlated_lognormal(np.random.default_rng(s), n, n, 16.0, m)
+         for s, m in zip(seeds, (1.0, 1e2, 1e4))]
+    return Workload("triple_%d" % n, n, n, 3, k, np.array([1.0, 0.2, 0.05]),
+                    _sym(3, {(0, 1): 5.0, (0, 2): 1.0, (1, 2): 20.0}),
+                    1.0 / 200, nsteps, _point_sources(n, 3, 2),
+                    [np.zeros((n, n))] * 3, seed=seeds[0])
+
+
+def precision_4096(n=4096, seed=3, nsteps=100):
+    """Dual continuum as dual_64 but k2 = 1e5 exp(0.5 N(0,1)), tau = 1/50."""
+    rng = np.random.default_rng(seed)
+    k1 = np.exp(rng.standard_normal((n, n)))
+    k2 = 1e5 * np.exp(0.5 * rng.standard_normal((n, n)))
+    return Workload("precision_%d" % n, n, n, 2, [k1, k2],
+                    np.array([1.0, 0.1]), _sym(2, {(0, 1): 10.0}), 1.0 / 50,
+                    nsteps, _point_sources(n, 2, 1), [np.zeros((n, n))] * 2,
+                    seed=seed)
+
+
+def fracture_instance(seed, n=None, L=None, tau=1.0 / 100, nsteps=100,
+                      sizes=(128, 256, 512, 1024)):
+    """One realisation with an embedded fracture continuum (the last one).
+
+    L in {2, 3} (p = 1/2) and n from `sizes` are drawn first unless given;
+    then the matrix field (log-normal, mean 1), for L = 3 a natural-fracture
+    field (log-normal, mean 1e2), then 20..200 random segments. Cells crossed
+    by a segment get k = 1e4 in the fracture continuum, all others 1e-2; the
+    fracture exchanges with every other continuum through
+    sigma_i = 10 * l_i / h, l_i the segment length inside cell i.
+    """
+    rng = np.random.default_rng(seed)
+    if L is None:
+        L = int(rng.integers(2, 4))
+    else:
+        rng.integers(2, 4)
+    if n is None:
+        n = int(sizes[int(rng.integers(0, len(sizes)))])
+    else:
+        rng.integers(0, len(sizes))
+    k = [correlated_lognormal(rng, n, n, 16.0, 1.0)]
+    if L == 3:
+        k.append(correlated_lognormal(rng, n, n, 16.0, 1e2))
+    ell = segment_lengths(random_segments(rng), n, n)
+    k.append(np.where(ell > 0.0, 1e4, 1e-2))
+    sig_f = 10.0 * ell * n
+    if L == 2:
+        c = np.array([1.0, 0.1])
+        sigma = np.zeros((2, 2))
+        sc = {(0, 1): sig_f}
+    else:
+        c = np.array([1.0, 0.2, 0.05])
+        sigma = _sym(3, {(0, 1): 5.0})
+        sc = {(0, 2): sig_f, (1, 2): sig_f.copy()}
+    return Workload("fracture_%d_L%d_s%d" % (n, L, seed), n, n, L, k, c, sigma,
+                    tau, nsteps, _point_sources(n, L, L - 1),
+                    [np.zeros((n, n))] * L, sigma_cell=sc, seed=seed)
+
+
+def batched_instances(count=256, base_seed=4000, sizes=(128, 256, 512, 1024),
+                      nsteps=100):
+    """Independent instances, instance b drawn with seed base_seed + b."""
+    return [fracture_instance(base_seed + b, sizes=sizes, nsteps=nsteps)
+            for b in range(count)]
+
+
+def nlmc_1024(n=1024, seed=5000, ncoarse=32, layers=2, nsteps=200):
+    """Dual-continuum fracture field at n^2, coarse grid ncoarse^2 with
+    `layers` oversampling layers, tau = 1/200."""
+    w = fracture_instance(seed, n=n, L=2, tau=1.0 / 200, nsteps=nsteps)
+    w.name = "nlmc_%d_c%d" % (n, ncoarse)
+    w.coarse = (ncoarse, ncoarse, layers)
+    return w
+
+
+def scaled(fn, n, **kw):
+    """The recipe of `fn` at another grid size (small parity cases)."""
+    return fn(n=n, **kw)
+
+
+def by_name(name):
+    table = {
+        "dual_64": dual_64,
+        "triple_1024": triple_1024,
+        "precision_4096": precision_4096,
+        "nlmc_1024": nlmc_1024,
+    }
+    return table[name]()
