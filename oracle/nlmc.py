@@ -188,9 +188,16 @@ class NLMC:
         return self._fact[key]
 
     def _solve(self, key, b):
+        """Dense LU plus two refinement sweeps with an extended-precision
+        residual (same reason as the fine-grid solves)."""
         Mt, f = self._lu(key)
+        Me = Mt.astype(np.longdouble)
+        be = np.asarray(b, dtype=np.float64).astype(np.longdouble)
         x = la.lu_solve(f, b)
-        return x + la.lu_solve(f, b - Mt @ x)
+        for _ in range(2):
+            r = be - Me @ x.astype(np.longdouble)
+            x = x + la.lu_solve(f, np.asarray(r, dtype=np.float64))
+        return x
 
     def step(self, pbar, Fbar, scheme="D"):
         n, L = self.Nc, self.fv.L

@@ -213,9 +213,10 @@ def test_splitting_error_first_order_in_tau():
 
 
 def test_oracle_forward_error_two_orderings():
-    """Self-accuracy: two fill-reducing orderings agree below the 1e-10
-    parity bar (measured about 2e-11 for the coupled three-continuum system at
-    64 x 64, whose constant mode is held only by the small mass term)."""
+    """Self-accuracy: two fill-reducing orderings agree far below the 1e-10
+    parity bar. With an FP64 refinement residual they differed by 2e-11 for
+    the coupled three-continuum system at 64 x 64 (constant mode held only by
+    the small mass term); the extended-precision residual closes the gap."""
     w = mi.triple_1024(n=64)
     oa = from_workload(w)
     ob = from_workload(w)
@@ -224,4 +225,4 @@ def test_oracle_forward_error_two_orderings():
     for scheme in ("coupled", "D"):
         pa = oa.run(w.p0, F, 3, scheme)
         pb = ob.run(w.p0, F, 3, scheme)
-        assert metrics.rel_l2(pa, pb) < 1e-10
+        assert metrics.rel_l2(pa, pb) < 1e-13
