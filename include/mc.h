@@ -1,0 +1,193 @@
+/*
+ * mc.h -- C ABI of the GB300 (sm_103a) decoupled multicontinuum solver.
+ *
+ * Method: Vasilyeva, "Efficient decoupling schemes for multiscale
+ * multicontinuum problems in fractured porous media" (arXiv 2209.01158).
+ *
+ *   Model (Section 2, Eq. mm, mm-bc): L pressures p_a on the unit square,
+ *     c_a dp_a/dt - div(k_a grad p_a) + sum_{b != a} sigma_ab (p_a - p_b) = f_a,
+ *     zero-flux boundaries.
+ *   Space (Section 3.1, Eqs. app-md, app, app-mc): two-point-flux finite
+ *     volumes on an nx x ny grid of square cells, h = 1/nx:
+ *       M_a = diag(c_a h^2), D_a: a_ii = sum_n T_in, a_ij = -T_ij with
+ *       T_ij = k_face |E|/d = k_face (harmonic mean of the two cells),
+ *       Q_ab = diag(sigma_ab,i h^2) (co-located continua), F_a cell-integrated.
+ *   Time (Section 3.2-3.3): coupled backward Euler (Eq. ct-mc) or the
+ *     decoupled D-, L-, U-schemes (Eq. si-mc): each continuum solves
+ *       (M_a/tau + D_a + sum_b Q_ab) p_a^n
+ *           = M_a/tau p_a^{n-1} + F_a + sum_b Q_ab p_b^{n-1 or n}.
+ *   Coarse scale (Section 4): NLMC basis (Eq. eq:basis), A_bar = R A R^T,
+ *     coupled (Eq. is-nlmc) and decoupled (Eq. si-nlmc) coarse stepping.
+ *
+ * Every linear system is solved on the GPU by matrix-free preconditioned
+ * conjugate gradients on the 5-point stencil, all continua of a step in one
+ * persistent kernel launch.
+ *
+ * Conventions for every call:
+ *   - Field arrays are nx*ny doubles, cell (i, j) at index j*nx + i (x fastest).
+ *   - Host arrays passed in are copied during the call; the caller keeps them.
+ *   - Outputs go to caller-provided host buffers unless stated otherwise.
+ *   - Every call returns mc_status; no call throws or aborts. On failure the
+ *     context keeps its previous state where stated, and mc_last_error() gives
+ *     a one-line explanation.
+ *   - A context is bound to the CUDA device current at mc_setup and to one
+ *     stream; calls on one context must not run concurrently from two threads.
+ *   - All work is queued on the context's stream; calls that return host data
+ *     synchronise that stream.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_MAX_CONTINUA 4
+
+typedef struct mc_ctx mc_ctx;
+typedef struct mc_nlmc mc_nlmc;
+
+typedef enum {
+  MC_OK = 0,
+  MC_E_ARG = 1,        /* invalid argument (sizes, NULL, NaN/negative data) */
+  MC_E_ALLOC = 2,      /* device or host allocation failed */
+  MC_E_CUDA = 3,       /* a CUDA runtime call failed */
+  MC_E_NOCONV = 4,     /* a solve hit max_iter before rtol */
+  MC_E_TIMEOUT = 5,    /* a device grid barrier exceeded its spin limit */
+  MC_E_STATE = 6,      /* call not valid in the current state */
+  MC_E_BREAKDOWN = 7   /* PCG breakdown: (p, A p) <= 0 or not finite */
+} mc_status;
+
+typedef struct {
+  int32_t nx, ny;      /* cells along x and y; h = 1/nx (square cells) */
+} mc_grid;
+
+enum { MC_PREC_FP64 = 0, MC_PREC_FP32_IR = 1, MC_PREC_BF16T_IR = 2 };
+enum { MC_PRECOND_JACOBI = 0 };
+enum { MC_SCHEME_COUPLED = -1, MC_SCHEME_D = 0, MC_SCHEME_L = 1, MC_SCHEME_U = 2 };
+
+typedef struct {
+  int32_t precision;   /* MC_PREC_*: FP64 PCG, or FP32 / BF16-transmissibility
+                          inner PCG inside FP64 iterative refinement */
+  int32_t precond;     /* MC_PRECOND_JACOBI */
+  int32_t max_iter;    /* PCG iterations per solve (inner iterations for IR) */
+  int32_t ir_max;      /* maximum refinement sweeps per solve (IR forms) */
+  double rtol;         /* stop when ||b - A x||_2 <= rtol ||b||_2 (FP64) */
+  double inner_rtol;   /* inner PCG relative target of each IR sweep */
+  int64_t spin_limit;  /* polls of a grid barrier before MC_E_TIMEOUT */
+  int32_t blocks;      /* persistent CTAs (0: one per SM x occupancy) */
+  int32_t threads;     /* threads per CTA (0: default 512) */
+} mc_opts;
+
+typedef struct {
+  int32_t steps_done;                    /* steps completed by the call */
+  int32_t status;                        /* mc_status of the device run */
+  int64_t iters[MC_MAX_CONTINUA];        /* PCG iterations summed over the
+                                            call's steps (coupled: iters[0]) */
+  int32_t max_iters[MC_MAX_CONTINUA];    /* largest single-solve count */
+  int32_t ir_sweeps;                     /* refinement sweeps summed (IR) */
+  int32_t reserved;
+  double rel_residual[MC_MAX_CONTINUA];  /* ||r||/||b|| of the last solve */
+  double mass_defect;                    /* last step: |LHS - RHS| / scale of
+                                            the scheme's mass identity */
+} mc_stats;
+
+/* Fill *o with the defaults (FP64, Jacobi, rtol 1e-12, max_iter 100000). */
+mc_status mc_default_opts(mc_opts* o);
+
+/*
+ * mc_setup -- build a context: coefficients and state on the device.
+ *   g          grid (nx, ny >= 1).
+ *   L          number of continua, 1..MC_MAX_CONTINUA.
+ *   k          L host arrays of nx*ny permeabilities (>= 0, finite).
+ *   c          L values c_a > 0 (Eq. mm; M_a = c_a h^2).
+ *   sigma      L*L row-major symmetric exchange coefficients per unit area
+ *              (diagonal ignored), or NULL for none.
+ *   sigma_cell L*(L-1)/2 host pointers, one per pair (a < b) in the order
+ *              (0,1),(0,2),..,(0,L-1),(1,2),..; each NULL or nx*ny per-cell
+ *              values that replace sigma[a][b] for that pair. May be NULL.
+ *   tau        time step > 0.
+ *   opts       NULL for defaults.
+ *   stream     cudaStream_t to queue all work on (NULL: legacy default).
+ * The state p starts at 0 and the sources at 0.
+ * Section 3.1: T_ij, a_ij, m, q entries; Section 3.3: diagonal of
+ * M_a/tau + A0_aa used by the Jacobi preconditioner.
+ */
+mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k,
+                   const double* c, const double* sigma,
+                   const double* const* sigma_cell, double tau,
+                   const mc_opts* opts, void* stream, mc_ctx** out);
+
+/* Replace opts (precision, tolerances, launch shape) of a live context. */
+mc_status mc_set_opts(mc_ctx* ctx, const mc_opts* opts);
+
+/* F_a (cell-integrated source, Eq. app-mc: F = f |cell|), host nx*ny. */
+mc_status mc_set_source(mc_ctx* ctx, int32_t alpha, const double* F);
+
+/* Copy L host arrays into the state p^n. */
+mc_status mc_set_state(mc_ctx* ctx, const double* const* p);
+
+/* Copy the state p^n into L host arrays. Synchronises the stream. */
+mc_status mc_get_state(mc_ctx* ctx, double* const* p);
+
+/* Device pointer of continuum alpha's state (nx*ny doubles, owned by the
+ * context, valid until mc_destroy). Lets a caller keep inputs resident. */
+mc_status mc_state_device(mc_ctx* ctx, int32_t alpha, double** dev);
+
+/*
+ * mc_step_decoupled -- nsteps steps of the D- (Eq. si-mc, Section 3.3),
+ * L- or U-scheme (A0 lower / upper block triangular; continua solved in
+ * index / reverse index order, index order = ascending permeability).
+ * D-scheme: every continuum's right-hand side
+ *   M_a/tau p_a^{n-1} + F_a + sum_b Q_ab p_b^{n-1}
+ * is assembled in one fused pass and all L solves run concurrently.
+ * Whole call is one persistent kernel launch. On MC_E_NOCONV / MC_E_BREAKDOWN
+ * / MC_E_TIMEOUT the state holds the last completed step (steps_done).
+ * stats may be NULL. Synchronises the stream.
+ */
+mc_status mc_step_decoupled(mc_ctx* ctx, int32_t scheme, int32_t nsteps,
+                            mc_stats* stats);
+
+/*
+ * mc_step_coupled -- nsteps steps of backward Euler on the full coupled
+ * system (M/tau + D + Q) p^n = M/tau p^{n-1} + F (Eq. ct-mc, Section 3.2),
+ * one PCG over all L*nx*ny unknowns per step. Same error contract as
+ * mc_step_decoupled.
+ */
+mc_status mc_step_coupled(mc_ctx* ctx, int32_t nsteps, mc_stats* stats);
+
+/*
+ * mc_get_coefficients -- copy the device coefficients of continuum alpha:
+ * TE[j*nx+i] (face to (i+1,j), 0 on the last column), TN[j*nx+i] (face to
+ * (i,j+1), 0 on the last row), diag = c h^2/tau + sum_b q_ab + sum_faces T
+ * (diagonal of M_a/tau + A0_aa). Any output pointer may be NULL.
+ */
+mc_status mc_get_coefficients(mc_ctx* ctx, int32_t alpha, double* TE,
+                              double* TN, double* diag);
+
+/* Apply the operator of one step to L host vectors x: y_a = (M_a/tau +
+ * D_a + sum_b Q_ab) x_a for the decoupled schemes (scheme >= 0), or
+ * y = (M/tau + D + Q) x over all continua (MC_SCHEME_COUPLED). */
+mc_status mc_apply(mc_ctx* ctx, int32_t scheme, const double* const* x,
+                   double* const* y);
+
+/* D-scheme right-hand sides of the current state into L host arrays:
+ * b_a = M_a/tau p_a + F_a + sum_b Q_ab p_b. */
+mc_status mc_rhs_decoupled(mc_ctx* ctx, double* const* b);
+
+/* Bytes of device memory the context holds. */
+mc_status mc_device_bytes(const mc_ctx* ctx, int64_t* bytes);
+
+void mc_destroy(mc_ctx* ctx);
+
+/* Last error text of ctx (or of the last failed mc_setup when ctx is NULL). */
+const char* mc_last_error(const mc_ctx* ctx);
+const char* mc_status_string(mc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MC_H */

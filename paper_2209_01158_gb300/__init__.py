@@ -1,0 +1,288 @@
+"""GB300 (sm_103a) decoupled multicontinuum time stepping.
+
+Python binding of libmc.so (include/mc.h): the functions below carry the C
+names and only marshal arguments; every step of the method runs in the CUDA
+kernels of the library. Host arrays may be numpy float64 arrays or CPU torch
+float64 tensors (pinned tensors give asynchronous-capable copies); streams may
+be given as a torch.cuda.Stream or a raw cudaStream_t integer.
+"""
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as N
+from ._native import (MC_SCHEME_COUPLED, MC_SCHEME_D, MC_SCHEME_L, MC_SCHEME_U,
+                      MC_PREC_FP64, MC_PREC_FP32_IR, MC_PREC_BF16T_IR, MC_MAX_CONTINUA)
+
+SCHEMES = {"coupled": MC_SCHEME_COUPLED, "D": MC_SCHEME_D, "L": MC_SCHEME_L, "U": MC_SCHEME_U}
+
+
+class MCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d)" % (msg, status))
+        self.status = status
+
+
+def _lib():
+    return N.load()
+
+
+def _check(st, ctx=None):
+    if st != N.MC_OK:
+        lib = _lib()
+        msg = lib.mc_last_error(ctx).decode() if ctx is not None else lib.mc_last_error(None).decode()
+        raise MCError(st, msg or lib.mc_status_string(st).decode())
+
+
+def _dptr(x, n=None, writable=False):
+    """(double*, keepalive) for a host array: numpy float64 or CPU torch float64."""
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if x.is_cuda:
+            raise ValueError("host buffer expected, got a CUDA tensor")
+        if str(x.dtype) != "torch.float64" or not x.is_contiguous():
+            raise ValueError("torch host buffers must be contiguous float64")
+        if n is not None and x.numel() != n:
+            raise ValueError("buffer has %d values, need %d" % (x.numel(), n))
+        return C.cast(C.c_void_p(x.data_ptr()), N.dp), x
+    a = np.asarray(x)
+    if writable:
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise ValueError("output arrays must be C-contiguous float64")
+    else:
+        a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError("array has %d values, need %d" % (a.size, n))
+    return a.ctypes.data_as(N.dp), a
+
+
+def _dptr_list(xs, n, writable=False):
+    ptrs, keep = [], []
+    for x in xs:
+        p, k = _dptr(x, n, writable)
+        ptrs.append(p)
+        keep.append(k)
+    arr = (N.dp * len(ptrs))(*ptrs)
+    return arr, keep
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def mc_default_opts():
+    o = N.mc_opts()
+    _check(_lib().mc_default_opts(C.byref(o)))
+    return o
+
+
+def mc_setup(nx, ny, k, c, sigma=None, sigma_cell=None, tau=1.0, opts=None, stream=None):
+    """Returns an opaque context handle (c_void_p). sigma: L x L array or None;
+    sigma_cell: dict {(a, b): array} (a < b) or a list in pair order or None."""
+    L = len(k)
+    n = int(nx) * int(ny)
+    kk, keep_k = _dptr_list(k, n)
+    cc = np.ascontiguousarray(c, dtype=np.float64)
+    if cc.size != L:
+        raise ValueError("c needs L values")
+    sg = None
+    if sigma is not None:
+        sg = np.ascontiguousarray(sigma, dtype=np.float64).reshape(L, L)
+    sc_arr = None
+    keep_sc = []
+    if sigma_cell:
+        pairs = [(a, b) for a in range(L) for b in range(a + 1, L)]
+        if isinstance(sigma_cell, dict):
+            seq = [sigma_cell.get(pq) for pq in pairs]
+        else:
+            seq = list(sigma_cell)
+        ptrs = []
+        for v in seq:
+            if v is None:
+                ptrs.append(N.dp())
+            else:
+                p, kp = _dptr(v, n)
+                ptrs.append(p)
+                keep_sc.append(kp)
+        sc_arr = (N.dp * len(ptrs))(*ptrs)
+    g = N.mc_grid(int(nx), int(ny))
+    out = C.c_void_p()
+    st = _lib().mc_setup(C.byref(g), L, kk, cc.ctypes.data_as(N.dp),
+                         sg.ctypes.data_as(N.dp) if sg is not None else None,
+                         sc_arr, float(tau), C.byref(opts) if opts is not None else None,
+                         _stream_handle(stream), C.byref(out))
+    _check(st)
+    return out
+
+
+def mc_set_opts(ctx, opts):
+    _check(_lib().mc_set_opts(ctx, C.byref(opts)), ctx)
+
+
+def mc_set_source(ctx, alpha, F, n=None):
+    p, keep = _dptr(F, n)
+    _check(_lib().mc_set_source(ctx, int(alpha), p), ctx)
+
+
+def mc_set_state(ctx, p, n=None):
+    arr, keep = _dptr_list(p, n)
+    _check(_lib().mc_set_state(ctx, arr), ctx)
+
+
+def mc_get_state(ctx, out):
+    """Fill the L preallocated host buffers `out` with the state."""
+    arr, keep = _dptr_list(out, None, writable=True)
+    _check(_lib().mc_get_state(ctx, arr), ctx)
+    return out
+
+
+def mc_state_device(ctx, alpha):
+    ptr = C.c_void_p()
+    _check(_lib().mc_state_device(ctx, int(alpha), C.byref(ptr)), ctx)
+    return ptr.value
+
+
+def _stats_dict(s, L):
+    return {
+        "steps_done": s.steps_done, "status": s.status,
+        "iters": [int(s.iters[a]) for a in range(L)],
+        "max_iters": [int(s.max_iters[a]) for a in range(L)],
+        "ir_sweeps": int(s.ir_sweeps),
+        "rel_residual": [float(s.rel_residual[a]) for a in range(L)],
+        "mass_defect": float(s.mass_defect),
+    }
+
+
+def mc_step_decoupled(ctx, scheme, nsteps, L=MC_MAX_CONTINUA, check=True):
+    s = N.mc_stats()
+    st = _lib().mc_step_decoupled(ctx, int(scheme), int(nsteps), C.byref(s))
+    d = _stats_dict(s, L)
+    d["return"] = st
+    if check:
+        _check(st, ctx)
+    return d
+
+
+def mc_step_coupled(ctx, nsteps, L=MC_MAX_CONTINUA, check=True):
+    s = N.mc_stats()
+    st = _lib().mc_step_coupled(ctx, int(nsteps), C.byref(s))
+    d = _stats_dict(s, L)
+    d["return"] = st
+    if check:
+        _check(st, ctx)
+    return d
+
+
+def mc_get_coefficients(ctx, alpha, n):
+    TE, TN, dg = np.empty(n), np.empty(n), np.empty(n)
+    _check(_lib().mc_get_coefficients(ctx, int(alpha), TE.ctypes.data_as(N.dp),
+                                      TN.ctypes.data_as(N.dp), dg.ctypes.data_as(N.dp)), ctx)
+    return TE, TN, dg
+
+
+def mc_apply(ctx, scheme, x, n):
+    xs, kx = _dptr_list(x, n)
+    ys = [np.empty(n) for _ in x]
+    yy, ky = _dptr_list(ys, n, writable=True)
+    _check(_lib().mc_apply(ctx, int(scheme), xs, yy), ctx)
+    return ys
+
+
+def mc_rhs_decoupled(ctx, L, n):
+    bs = [np.empty(n) for _ in range(L)]
+    bb, kb = _dptr_list(bs, n, writable=True)
+    _check(_lib().mc_rhs_decoupled(ctx, bb), ctx)
+    return bs
+
+
+def mc_device_bytes(ctx):
+    v = C.c_int64()
+    _check(_lib().mc_device_bytes(ctx, C.byref(v)), ctx)
+    return v.value
+
+
+def mc_destroy(ctx):
+    if ctx:
+        _lib().mc_destroy(ctx)
+
+
+class Context:
+    """Owning wrapper around an mc_ctx for one workload on one stream."""
+
+    def __init__(self, nx, ny, k, c, sigma=None, sigma_cell=None, tau=1.0, opts=None,
+                 stream=None):
+        self.nx, self.ny, self.L = int(nx), int(ny), len(k)
+        self.n = self.nx * self.ny
+        self._ctx = mc_setup(nx, ny, k, c, sigma, sigma_cell, tau, opts, stream)
+
+    @classmethod
+    def from_workload(cls, w, opts=None, stream=None):
+        ctx = cls(w.nx, w.ny, [np.ravel(x) for x in w.k], w.c, w.sigma,
+                  {kk: np.ravel(v) for kk, v in w.sigma_cell.items()} or None,
+                  w.tau, opts, stream)
+        for a in range(w.L):
+            ctx.set_source(a, w.F[a])
+        ctx.set_state(w.p0)
+        return ctx
+
+    @property
+    def handle(self):
+        return self._ctx
+
+    def set_opts(self, opts):
+        mc_set_opts(self._ctx, opts)
+
+    def set_source(self, alpha, F):
+        mc_set_source(self._ctx, alpha, np.ravel(F) if not hasattr(F, "data_ptr") else F, self.n)
+
+    def set_state(self, p):
+        mc_set_state(self._ctx, [np.ravel(x) if not hasattr(x, "data_ptr") else x for x in p],
+                     self.n)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = [np.empty(self.n) for _ in range(self.L)]
+        return mc_get_state(self._ctx, out)
+
+    def step_decoupled(self, scheme="D", nsteps=1, check=True):
+        sc = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+        return mc_step_decoupled(self._ctx, sc, nsteps, self.L, check)
+
+    def step_coupled(self, nsteps=1, check=True):
+        return mc_step_coupled(self._ctx, nsteps, self.L, check)
+
+    def step(self, scheme, nsteps=1, check=True):
+        if scheme == "coupled" or scheme == MC_SCHEME_COUPLED:
+            return self.step_coupled(nsteps, check)
+        return self.step_decoupled(scheme, nsteps, check)
+
+    def coefficients(self, alpha):
+        return mc_get_coefficients(self._ctx, alpha, self.n)
+
+    def apply(self, scheme, x):
+        sc = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+        return mc_apply(self._ctx, sc, [np.ravel(v) for v in x], self.n)
+
+    def rhs_decoupled(self):
+        return mc_rhs_decoupled(self._ctx, self.L, self.n)
+
+    def state_device(self, alpha):
+        return mc_state_device(self._ctx, alpha)
+
+    def device_bytes(self):
+        return mc_device_bytes(self._ctx)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            mc_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

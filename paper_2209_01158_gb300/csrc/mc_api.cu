@@ -1,0 +1,441 @@
+// C ABI of libmc.so: context life cycle, host <-> device copies, and the
+// step entry points that launch the persistent time-stepping kernel.
+
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "mc_internal.h"
+
+namespace {
+
+thread_local std::string g_setup_err;
+
+mc_status set_err(mc_ctx* ctx, mc_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg; else g_setup_err = msg;
+  return s;
+}
+
+mc_status cuda_err(mc_ctx* ctx, const char* what, cudaError_t e) {
+  return set_err(ctx, MC_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                        \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return cuda_err(ctx, #call, e_);             \
+  } while (0)
+
+bool finite_nonneg(const double* x, long long n) {
+  for (long long i = 0; i < n; ++i)
+    if (!(x[i] >= 0.0) || !isfinite(x[i])) return false;
+  return true;
+}
+
+void free_all(mc_ctx* ctx) {
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+}
+
+int launch_threads(const mc_ctx* ctx) { return ctx->opts.threads > 0 ? ctx->opts.threads : 512; }
+
+int launch_blocks(const mc_ctx* ctx) {
+  const int maxb = mc_step_max_blocks(ctx->L, launch_threads(ctx), ctx->num_sms);
+  int b = ctx->opts.blocks > 0 ? ctx->opts.blocks : maxb;
+  if (b > maxb) b = maxb;
+  return b;
+}
+
+mc_status check_opts(const mc_opts* o, std::string* why) {
+  if (o->precision < MC_PREC_FP64 || o->precision > MC_PREC_BF16T_IR) { *why = "precision"; return MC_E_ARG; }
+  if (o->precond != MC_PRECOND_JACOBI) { *why = "precond"; return MC_E_ARG; }
+  if (o->max_iter < 1) { *why = "max_iter < 1"; return MC_E_ARG; }
+  if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) { *why = "rtol must be in (0, 1)"; return MC_E_ARG; }
+  if (o->spin_limit < 1) { *why = "spin_limit < 1"; return MC_E_ARG; }
+  if (o->threads != 0 && o->threads != 512) { *why = "threads must be 0 or 512"; return MC_E_ARG; }
+  if (o->blocks < 0) { *why = "blocks < 0"; return MC_E_ARG; }
+  return MC_OK;
+}
+
+}  // namespace
+
+cudaError_t mc_alloc(mc_ctx* ctx, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 8;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) return e;
+  ctx->allocs.push_back(*ptr);
+  ctx->bytes += (int64_t)bytes;
+  return cudaMemset(*ptr, 0, bytes);
+}
+
+void mc_fill_params(const mc_ctx* ctx, StepParams* sp, int scheme, int nsteps) {
+  memset(sp, 0, sizeof(*sp));
+  sp->nx = ctx->nx;
+  sp->ny = ctx->ny;
+  sp->L = ctx->L;
+  sp->N = ctx->N;
+  sp->scheme = scheme;
+  sp->nsteps = nsteps;
+  sp->max_iter = ctx->opts.max_iter;
+  sp->rtol = ctx->opts.rtol;
+  sp->tau = ctx->tau;
+  const double area = ctx->h * ctx->h;
+  for (int a = 0; a < ctx->L; ++a) {
+    sp->mass[a] = ctx->c[a] * area;
+    sp->mtau[a] = ctx->c[a] * area / ctx->tau;
+    double dc = sp->mtau[a];
+    for (int b = 0; b < ctx->L; ++b) {
+      sp->qconst[a][b] = ctx->sigma[a][b] * area;
+      sp->qcell[a][b] = ctx->qcell[a][b];
+      if (b != a) dc += sp->qconst[a][b];
+    }
+    sp->diagc_const[a] = dc;
+    sp->diagc[a] = ctx->diagc[a];
+    sp->TE[a] = ctx->TE[a];
+    sp->TN[a] = ctx->TN[a];
+    sp->invd[a] = ctx->invd[a];
+    sp->F[a] = ctx->F[a];
+    sp->p[a] = ctx->p[a];
+    sp->pprev[a] = ctx->pprev[a];
+    sp->r[a] = ctx->r[a];
+    sp->P[0][a] = ctx->P[0][a];
+    sp->P[1][a] = ctx->P[1][a];
+    sp->q[a] = ctx->q[a];
+  }
+  sp->partials = ctx->partials;
+  sp->bar_count = ctx->bar;
+  sp->bar_gen = ctx->bar + 32;
+  sp->status = ctx->dstatus;
+  sp->steps_done = ctx->dsteps;
+  sp->iters = ctx->diters;
+  sp->max_iters = ctx->dmaxit;
+  sp->relres = ctx->drelres;
+  sp->mass_defect = ctx->dmass;
+  sp->spin_limit = ctx->opts.spin_limit;
+}
+
+extern "C" {
+
+mc_status mc_default_opts(mc_opts* o) {
+  if (!o) return MC_E_ARG;
+  memset(o, 0, sizeof(*o));
+  o->precision = MC_PREC_FP64;
+  o->precond = MC_PRECOND_JACOBI;
+  o->max_iter = 100000;
+  o->ir_max = 50;
+  o->rtol = 1e-12;
+  o->inner_rtol = 1e-4;
+  o->spin_limit = 2000000;
+  o->blocks = 0;
+  o->threads = 0;
+  return MC_OK;
+}
+
+const char* mc_status_string(mc_status s) {
+  switch (s) {
+    case MC_OK: return "ok";
+    case MC_E_ARG: return "invalid argument";
+    case MC_E_ALLOC: return "allocation failed";
+    case MC_E_CUDA: return "CUDA error";
+    case MC_E_NOCONV: return "no convergence within max_iter";
+    case MC_E_TIMEOUT: return "device barrier timeout";
+    case MC_E_STATE: return "invalid state";
+    case MC_E_BREAKDOWN: return "PCG breakdown";
+  }
+  return "unknown status";
+}
+
+const char* mc_last_error(const mc_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_setup_err.c_str();
+}
+
+mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const double* c,
+                   const double* sigma, const double* const* sigma_cell, double tau,
+                   const mc_opts* opts, void* stream, mc_ctx** out) {
+  mc_ctx* ctx = nullptr;
+  if (!out) return set_err(nullptr, MC_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (!g || g->nx < 1 || g->ny < 1) return set_err(nullptr, MC_E_ARG, "grid must have nx, ny >= 1");
+  if ((long long)g->nx * g->ny > (1LL << 31)) return set_err(nullptr, MC_E_ARG, "grid larger than 2^31 cells");
+  if (L < 1 || L > MC_MAX_CONTINUA) return set_err(nullptr, MC_E_ARG, "L must be in 1..MC_MAX_CONTINUA");
+  if (!k || !c) return set_err(nullptr, MC_E_ARG, "k and c are required");
+  if (!(tau > 0.0) || !isfinite(tau)) return set_err(nullptr, MC_E_ARG, "tau must be > 0 and finite");
+  const long long N = (long long)g->nx * g->ny;
+  for (int a = 0; a < L; ++a) {
+    if (!(c[a] > 0.0) || !isfinite(c[a])) return set_err(nullptr, MC_E_ARG, "c must be > 0 and finite");
+    if (!k[a]) return set_err(nullptr, MC_E_ARG, "k[a] is NULL");
+    if (!finite_nonneg(k[a], N)) return set_err(nullptr, MC_E_ARG, "k must be finite and >= 0");
+  }
+  if (sigma) {
+    for (int a = 0; a < L; ++a)
+      for (int b = 0; b < L; ++b) {
+        if (a == b) continue;
+        const double s = sigma[a * L + b];
+        if (!(s >= 0.0) || !isfinite(s)) return set_err(nullptr, MC_E_ARG, "sigma must be finite and >= 0");
+        if (s != sigma[b * L + a]) return set_err(nullptr, MC_E_ARG, "sigma must be symmetric");
+      }
+  }
+  if (sigma_cell) {
+    int pi = 0;
+    for (int a = 0; a < L; ++a)
+      for (int b = a + 1; b < L; ++b, ++pi)
+        if (sigma_cell[pi] && !finite_nonneg(sigma_cell[pi], N))
+          return set_err(nullptr, MC_E_ARG, "sigma_cell must be finite and >= 0");
+  }
+  mc_opts o;
+  mc_default_opts(&o);
+  if (opts) o = *opts;
+  std::string why;
+  if (check_opts(&o, &why) != MC_OK) return set_err(nullptr, MC_E_ARG, "opts: " + why);
+
+  ctx = new (std::nothrow) mc_ctx();
+  if (!ctx) return set_err(nullptr, MC_E_ALLOC, "host allocation failed");
+  ctx->nx = g->nx;
+  ctx->ny = g->ny;
+  ctx->L = L;
+  ctx->N = N;
+  ctx->h = 1.0 / g->nx;
+  ctx->tau = tau;
+  ctx->opts = o;
+  ctx->stream = (cudaStream_t)stream;
+  for (int a = 0; a < L; ++a) {
+    ctx->c[a] = c[a];
+    for (int b = 0; b < L; ++b) ctx->sigma[a][b] = (sigma && a != b) ? sigma[a * L + b] : 0.0;
+  }
+  auto bail = [&](mc_status s) {
+    g_setup_err = ctx->err;
+    free_all(ctx);
+    delete ctx;
+    return s;
+  };
+  cudaError_t e;
+#define CKS(call)                                                   \
+  do {                                                              \
+    e = (call);                                                     \
+    if (e != cudaSuccess) {                                         \
+      cuda_err(ctx, #call, e);                                      \
+      return bail(e == cudaErrorMemoryAllocation ? MC_E_ALLOC : MC_E_CUDA); \
+    }                                                               \
+  } while (0)
+  CKS(cudaGetDevice(&ctx->device));
+  CKS(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  const size_t fb = (size_t)N * sizeof(double);
+  // Per-cell exchange arrays (sigma first, scaled to q = sigma h^2 on device).
+  if (sigma_cell) {
+    int pi = 0;
+    for (int a = 0; a < L; ++a)
+      for (int b = a + 1; b < L; ++b, ++pi) {
+        if (!sigma_cell[pi]) continue;
+        CKS(mc_alloc(ctx, (void**)&ctx->qcell[a][b], fb));
+        ctx->qcell[b][a] = ctx->qcell[a][b];
+        CKS(cudaMemcpyAsync(ctx->qcell[a][b], sigma_cell[pi], fb, cudaMemcpyHostToDevice, ctx->stream));
+      }
+  }
+  for (int a = 0; a < L; ++a) {
+    bool percell = false;
+    for (int b = 0; b < L; ++b) percell |= (ctx->qcell[a][b] != nullptr);
+    CKS(mc_alloc(ctx, (void**)&ctx->TE[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->TN[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->invd[a], fb));
+    if (percell) CKS(mc_alloc(ctx, (void**)&ctx->diagc[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->F[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->p[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->pprev[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->r[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->P[0][a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->P[1][a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->q[a], fb));
+  }
+  const int maxb = mc_step_max_blocks(L, 512, ctx->num_sms);
+  if (maxb < 1) {
+    cuda_err(ctx, "occupancy query", cudaGetLastError());
+    return bail(MC_E_CUDA);
+  }
+  ctx->partials_len = (size_t)2 * 4 * MCL * maxb;
+  CKS(mc_alloc(ctx, (void**)&ctx->partials, ctx->partials_len * sizeof(double)));
+  CKS(mc_alloc(ctx, (void**)&ctx->bar, 96 * sizeof(unsigned)));
+  CKS(mc_alloc(ctx, (void**)&ctx->dstatus, sizeof(int)));
+  CKS(mc_alloc(ctx, (void**)&ctx->dsteps, sizeof(int)));
+  CKS(mc_alloc(ctx, (void**)&ctx->diters, MCL * sizeof(long long)));
+  CKS(mc_alloc(ctx, (void**)&ctx->dmaxit, MCL * sizeof(int)));
+  CKS(mc_alloc(ctx, (void**)&ctx->drelres, MCL * sizeof(double)));
+  CKS(mc_alloc(ctx, (void**)&ctx->dmass, sizeof(double)));
+  // Coefficients: k goes through the r buffer (work space, free until the
+  // first step) into TE / TN.
+  for (int a = 0; a < L; ++a) {
+    CKS(cudaMemcpyAsync(ctx->r[a], k[a], fb, cudaMemcpyHostToDevice, ctx->stream));
+    CKS(mc_launch_setup(ctx, a, ctx->r[a]));
+  }
+  for (int a = 0; a < L; ++a) CKS(mc_launch_diag(ctx, a));
+  CKS(cudaStreamSynchronize(ctx->stream));
+#undef CKS
+  *out = ctx;
+  return MC_OK;
+}
+
+void mc_destroy(mc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  delete ctx;
+}
+
+mc_status mc_set_opts(mc_ctx* ctx, const mc_opts* opts) {
+  if (!ctx || !opts) return MC_E_ARG;
+  std::string why;
+  if (check_opts(opts, &why) != MC_OK) return set_err(ctx, MC_E_ARG, "opts: " + why);
+  ctx->opts = *opts;
+  return MC_OK;
+}
+
+mc_status mc_set_source(mc_ctx* ctx, int32_t alpha, const double* F) {
+  if (!ctx) return MC_E_ARG;
+  if (alpha < 0 || alpha >= ctx->L || !F) return set_err(ctx, MC_E_ARG, "bad alpha or F");
+  for (long long i = 0; i < ctx->N; ++i)
+    if (!isfinite(F[i])) return set_err(ctx, MC_E_ARG, "F must be finite");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpyAsync(ctx->F[alpha], F, ctx->N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MC_OK;
+}
+
+mc_status mc_set_state(mc_ctx* ctx, const double* const* p) {
+  if (!ctx) return MC_E_ARG;
+  if (!p) return set_err(ctx, MC_E_ARG, "p is NULL");
+  for (int a = 0; a < ctx->L; ++a)
+    if (!p[a]) return set_err(ctx, MC_E_ARG, "p[a] is NULL");
+  CK(cudaSetDevice(ctx->device));
+  for (int a = 0; a < ctx->L; ++a)
+    CK(cudaMemcpyAsync(ctx->p[a], p[a], ctx->N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MC_OK;
+}
+
+mc_status mc_get_state(mc_ctx* ctx, double* const* p) {
+  if (!ctx) return MC_E_ARG;
+  if (!p) return set_err(ctx, MC_E_ARG, "p is NULL");
+  for (int a = 0; a < ctx->L; ++a)
+    if (!p[a]) return set_err(ctx, MC_E_ARG, "p[a] is NULL");
+  CK(cudaSetDevice(ctx->device));
+  for (int a = 0; a < ctx->L; ++a)
+    CK(cudaMemcpyAsync(p[a], ctx->p[a], ctx->N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MC_OK;
+}
+
+mc_status mc_state_device(mc_ctx* ctx, int32_t alpha, double** dev) {
+  if (!ctx || !dev || alpha < 0 || alpha >= ctx->L) return MC_E_ARG;
+  *dev = ctx->p[alpha];
+  return MC_OK;
+}
+
+static mc_status run_steps(mc_ctx* ctx, int scheme, int nsteps, mc_stats* stats) {
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (nsteps < 0) return set_err(ctx, MC_E_ARG, "nsteps < 0");
+  if (ctx->opts.precision != MC_PREC_FP64)
+    return set_err(ctx, MC_E_ARG, "this precision form is not available for this entry point");
+  if (nsteps == 0) return MC_OK;
+  CK(cudaSetDevice(ctx->device));
+  StepParams sp;
+  mc_fill_params(ctx, &sp, scheme, nsteps);
+  CK(cudaMemsetAsync(ctx->bar, 0, 96 * sizeof(unsigned), ctx->stream));
+  CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->dsteps, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->diters, 0, MCL * sizeof(long long), ctx->stream));
+  CK(cudaMemsetAsync(ctx->dmaxit, 0, MCL * sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->drelres, 0, MCL * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->dmass, 0, sizeof(double), ctx->stream));
+  const int blocks = launch_blocks(ctx);
+  CK(mc_launch_steps(ctx, sp, blocks, launch_threads(ctx)));
+  int st = 0, done = 0;
+  mc_stats s;
+  memset(&s, 0, sizeof(s));
+  CK(cudaMemcpyAsync(&st, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&done, ctx->dsteps, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(s.iters, ctx->diters, MCL * sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(s.max_iters, ctx->dmaxit, MCL * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(s.rel_residual, ctx->drelres, MCL * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&s.mass_defect, ctx->dmass, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  s.steps_done = done;
+  s.status = st;
+  if (st != MC_OK) {
+    // Roll the state back to the start of the failed step.
+    for (int a = 0; a < ctx->L; ++a)
+      CK(cudaMemcpyAsync(ctx->p[a], ctx->pprev[a], ctx->N * sizeof(double), cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (stats) *stats = s;
+  if (st != MC_OK)
+    return set_err(ctx, (mc_status)st, std::string("step ") + std::to_string(done + 1) + ": " +
+                                           mc_status_string((mc_status)st));
+  return MC_OK;
+}
+
+mc_status mc_step_decoupled(mc_ctx* ctx, int32_t scheme, int32_t nsteps, mc_stats* stats) {
+  if (!ctx) return MC_E_ARG;
+  if (scheme != MC_SCHEME_D && scheme != MC_SCHEME_L && scheme != MC_SCHEME_U)
+    return set_err(ctx, MC_E_ARG, "scheme must be MC_SCHEME_D, _L or _U");
+  return run_steps(ctx, scheme, nsteps, stats);
+}
+
+mc_status mc_step_coupled(mc_ctx* ctx, int32_t nsteps, mc_stats* stats) {
+  if (!ctx) return MC_E_ARG;
+  return run_steps(ctx, MC_SCHEME_COUPLED, nsteps, stats);
+}
+
+mc_status mc_get_coefficients(mc_ctx* ctx, int32_t alpha, double* TE, double* TN, double* diag) {
+  if (!ctx || alpha < 0 || alpha >= ctx->L) return MC_E_ARG;
+  CK(cudaSetDevice(ctx->device));
+  const size_t fb = ctx->N * sizeof(double);
+  if (TE) CK(cudaMemcpyAsync(TE, ctx->TE[alpha], fb, cudaMemcpyDeviceToHost, ctx->stream));
+  if (TN) CK(cudaMemcpyAsync(TN, ctx->TN[alpha], fb, cudaMemcpyDeviceToHost, ctx->stream));
+  if (diag) CK(cudaMemcpyAsync(diag, ctx->invd[alpha], fb, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (diag)
+    for (long long i = 0; i < ctx->N; ++i) diag[i] = 1.0 / diag[i];
+  return MC_OK;
+}
+
+mc_status mc_apply(mc_ctx* ctx, int32_t scheme, const double* const* x, double* const* y) {
+  if (!ctx || !x || !y) return MC_E_ARG;
+  if (scheme != MC_SCHEME_COUPLED && (scheme < MC_SCHEME_D || scheme > MC_SCHEME_U))
+    return set_err(ctx, MC_E_ARG, "bad scheme");
+  CK(cudaSetDevice(ctx->device));
+  const size_t fb = ctx->N * sizeof(double);
+  // r and q are step work space: free between steps.
+  for (int a = 0; a < ctx->L; ++a) {
+    if (!x[a] || !y[a]) return set_err(ctx, MC_E_ARG, "x[a] / y[a] NULL");
+    CK(cudaMemcpyAsync(ctx->r[a], x[a], fb, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  CK(mc_launch_apply(ctx, scheme, ctx->r, ctx->q));
+  for (int a = 0; a < ctx->L; ++a)
+    CK(cudaMemcpyAsync(y[a], ctx->q[a], fb, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MC_OK;
+}
+
+mc_status mc_rhs_decoupled(mc_ctx* ctx, double* const* b) {
+  if (!ctx || !b) return MC_E_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(mc_launch_rhs(ctx, ctx->q));
+  for (int a = 0; a < ctx->L; ++a) {
+    if (!b[a]) return set_err(ctx, MC_E_ARG, "b[a] NULL");
+    CK(cudaMemcpyAsync(b[a], ctx->q[a], ctx->N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MC_OK;
+}
+
+mc_status mc_device_bytes(const mc_ctx* ctx, int64_t* bytes) {
+  if (!ctx || !bytes) return MC_E_ARG;
+  *bytes = ctx->bytes;
+  return MC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Internal declarations shared by the translation units of libmc.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mc.h"
+
+#define MCL MC_MAX_CONTINUA
+
+// Everything the persistent time-stepping kernel needs, passed by value.
+// Field pointers address nx*ny doubles, cell (i, j) at j*nx + i.
+struct StepParams {
+  int nx, ny, L;
+  long long N;
+  int scheme;          // MC_SCHEME_*
+  int nsteps;
+  int max_iter;
+  int tiles_x, tiles_y;  // stencil tiles per continuum
+  double rtol;
+  double tau;
+  double mtau[MCL];                // c_a h^2 / tau
+  double mass[MCL];                // c_a h^2
+  double qconst[MCL][MCL];         // sigma_ab h^2 where no per-cell array
+  const double* qcell[MCL][MCL];   // per-cell sigma_ab h^2 or nullptr
+  double diagc_const[MCL];         // c_a h^2/tau + sum_b q_ab (constant case)
+  const double* diagc[MCL];        // same per cell, or nullptr
+  const double* TE[MCL];
+  const double* TN[MCL];
+  const double* invd[MCL];
+  const double* F[MCL];
+  double* p[MCL];
+  double* pprev[MCL];
+  double* r[MCL];
+  double* P[2][MCL];
+  double* q[MCL];
+  double* partials;                // [2 slots][4 quantities][MCL][nblocks]
+  unsigned* bar_count;
+  unsigned* bar_gen;
+  int* status;                     // mc_status of the run (0 = OK)
+  int* steps_done;
+  long long* iters;                // [MCL]
+  int* max_iters;                  // [MCL]
+  double* relres;                  // [MCL]
+  double* mass_defect;             // [1]
+  long long spin_limit;
+};
+
+struct mc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int nx = 0, ny = 0, L = 0;
+  long long N = 0;
+  double h = 0, tau = 0;
+  double c[MCL] = {};
+  double sigma[MCL][MCL] = {};
+  mc_opts opts{};
+  int num_sms = 0;
+  // device buffers
+  double* TE[MCL] = {};
+  double* TN[MCL] = {};
+  double* invd[MCL] = {};
+  double* diagc[MCL] = {};
+  double* qcell[MCL][MCL] = {};
+  double* F[MCL] = {};
+  double* p[MCL] = {};
+  double* pprev[MCL] = {};
+  double* r[MCL] = {};
+  double* P[2][MCL] = {};
+  double* q[MCL] = {};
+  double* partials = nullptr;
+  size_t partials_len = 0;
+  unsigned* bar = nullptr;         // [0] count, [32] generation (own sector)
+  int* dstatus = nullptr;
+  int* dsteps = nullptr;
+  long long* diters = nullptr;
+  int* dmaxit = nullptr;
+  double* drelres = nullptr;
+  double* dmass = nullptr;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  std::string err;
+};
+
+// Allocation helper: zero-filled device buffer tracked by the context.
+cudaError_t mc_alloc(mc_ctx* ctx, void** ptr, size_t bytes);
+
+// Fill StepParams from a context (device pointers, constants).
+void mc_fill_params(const mc_ctx* ctx, StepParams* sp, int scheme, int nsteps);
+
+// Launch the persistent time-stepping kernel (mc_step.cu).
+cudaError_t mc_launch_steps(mc_ctx* ctx, const StepParams& sp, int blocks,
+                            int threads);
+
+// Maximum co-resident CTAs for the step kernel of this L (cooperative grid).
+int mc_step_max_blocks(int L, int threads, int num_sms);
+
+// Setup kernels (mc_setup_kernels.cu).
+cudaError_t mc_launch_setup(mc_ctx* ctx, int a, const double* k_dev);
+cudaError_t mc_launch_diag(mc_ctx* ctx, int a);
+cudaError_t mc_launch_apply(mc_ctx* ctx, int scheme, double* const* x,
+                            double* const* y);
+cudaError_t mc_launch_rhs(mc_ctx* ctx, double* const* b);

@@ -1,0 +1,207 @@
+// Coefficient set-up (once per context) and the standalone operator /
+// right-hand-side kernels used to inspect a context.
+//
+// Section 3.1, Eq. app-md: T_ij = k_face |E_ij| / d_ij. Cells are squares, so
+// |E| = d = h and T = k_face; the face value is the harmonic mean of the two
+// cell permeabilities (0 when both vanish). Boundary faces carry no
+// transmissibility (zero-flux condition, Eq. mm-bc). Exchange between
+// co-located continua: q_ab,i = sigma_ab,i |cell| = sigma_ab,i h^2.
+// Diagonal of M_a/tau + D_a + sum_b Q_ab (Section 3.3, D-scheme A0 block):
+//   d_i = c_a h^2 / tau + sum_b q_ab,i + sum over the four faces of T.
+
+#include "mc_internal.h"
+
+namespace {
+
+__global__ void faces_kernel(int nx, int ny, const double* __restrict__ k,
+                             double* __restrict__ TE, double* __restrict__ TN) {
+  const long long N = (long long)nx * ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int gx = (int)(i % nx), gy = (int)(i / nx);
+    const double kc = k[i];
+    double te = 0.0, tn = 0.0;
+    if (gx + 1 < nx) {
+      const double kn = k[i + 1];
+      const double s = kc + kn;
+      te = s > 0.0 ? 2.0 * kc * kn / s : 0.0;
+    }
+    if (gy + 1 < ny) {
+      const double kn = k[i + nx];
+      const double s = kc + kn;
+      tn = s > 0.0 ? 2.0 * kc * kn / s : 0.0;
+    }
+    TE[i] = te;
+    TN[i] = tn;
+  }
+}
+
+__global__ void scale_kernel(long long N, double* __restrict__ x, double s) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] *= s;
+}
+
+struct DiagArgs {
+  int nx, ny, L, a;
+  double mtau;
+  double qconst[MCL];
+  const double* qcell[MCL];
+  const double* TE;
+  const double* TN;
+  double* diagc;  // may be nullptr (constant case)
+  double* invd;
+};
+
+__global__ void diag_kernel(DiagArgs g) {
+  const long long N = (long long)g.nx * g.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int gx = (int)(i % g.nx), gy = (int)(i / g.nx);
+    double dc = g.mtau;
+    for (int b = 0; b < g.L; ++b) {
+      if (b == g.a) continue;
+      dc += g.qcell[b] ? g.qcell[b][i] : g.qconst[b];
+    }
+    double t = g.TE[i] + g.TN[i];
+    if (gx > 0) t += g.TE[i - 1];
+    if (gy > 0) t += g.TN[i - g.nx];
+    if (g.diagc) g.diagc[i] = dc;
+    g.invd[i] = 1.0 / (dc + t);
+  }
+}
+
+struct ApplyArgs {
+  int nx, ny, L;
+  bool coupled;
+  double mtau[MCL];
+  double qconst[MCL][MCL];
+  const double* qcell[MCL][MCL];
+  const double* TE[MCL];
+  const double* TN[MCL];
+  const double* x[MCL];
+  double* y[MCL];
+  const double* F[MCL];
+  bool rhs;  // y_a = mtau x_a + F_a + sum_b q_ab x_b instead of the operator
+};
+
+__device__ __forceinline__ double q_of(const ApplyArgs& g, int a, int b, long long i) {
+  return g.qcell[a][b] ? g.qcell[a][b][i] : g.qconst[a][b];
+}
+
+__global__ void apply_kernel(ApplyArgs g) {
+  const long long N = (long long)g.nx * g.ny;
+  const int nx = g.nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int gx = (int)(i % nx), gy = (int)(i / nx);
+    for (int a = 0; a < g.L; ++a) {
+      const double xc = g.x[a][i];
+      double v;
+      if (g.rhs) {
+        v = g.mtau[a] * xc + g.F[a][i];
+        for (int b = 0; b < g.L; ++b)
+          if (b != a) v += q_of(g, a, b, i) * g.x[b][i];
+      } else {
+        v = g.mtau[a] * xc;
+        if (gx + 1 < nx) v += g.TE[a][i] * (xc - g.x[a][i + 1]);
+        if (gx > 0) v += g.TE[a][i - 1] * (xc - g.x[a][i - 1]);
+        if (gy + 1 < g.ny) v += g.TN[a][i] * (xc - g.x[a][i + nx]);
+        if (gy > 0) v += g.TN[a][i - nx] * (xc - g.x[a][i - nx]);
+        for (int b = 0; b < g.L; ++b) {
+          if (b == a) continue;
+          const double qv = q_of(g, a, b, i);
+          v += qv * xc;
+          if (g.coupled) v -= qv * g.x[b][i];
+        }
+      }
+      g.y[a][i] = v;
+    }
+  }
+}
+
+int grid_for(long long N) {
+  long long b = (N + 255) / 256;
+  if (b > 4096) b = 4096;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t mc_launch_setup(mc_ctx* ctx, int a, const double* k_dev) {
+  const long long N = ctx->N;
+  const int blocks = grid_for(N);
+  faces_kernel<<<blocks, 256, 0, ctx->stream>>>(ctx->nx, ctx->ny, k_dev, ctx->TE[a], ctx->TN[a]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // Per-cell exchange arrays hold sigma on upload; scale them to q = sigma h^2
+  // once, when the lower-indexed continuum of the pair is set up.
+  for (int b = a + 1; b < ctx->L; ++b) {
+    if (ctx->qcell[a][b]) {
+      scale_kernel<<<blocks, 256, 0, ctx->stream>>>(N, ctx->qcell[a][b], ctx->h * ctx->h);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t mc_launch_diag(mc_ctx* ctx, int a) {
+  DiagArgs g{};
+  g.nx = ctx->nx;
+  g.ny = ctx->ny;
+  g.L = ctx->L;
+  g.a = a;
+  g.mtau = ctx->c[a] * ctx->h * ctx->h / ctx->tau;
+  for (int b = 0; b < ctx->L; ++b) {
+    g.qconst[b] = ctx->sigma[a][b] * ctx->h * ctx->h;
+    g.qcell[b] = ctx->qcell[a][b];
+  }
+  g.TE = ctx->TE[a];
+  g.TN = ctx->TN[a];
+  g.diagc = ctx->diagc[a];
+  g.invd = ctx->invd[a];
+  diag_kernel<<<grid_for(ctx->N), 256, 0, ctx->stream>>>(g);
+  return cudaGetLastError();
+}
+
+static void fill_apply(const mc_ctx* ctx, ApplyArgs* g) {
+  g->nx = ctx->nx;
+  g->ny = ctx->ny;
+  g->L = ctx->L;
+  for (int a = 0; a < ctx->L; ++a) {
+    g->mtau[a] = ctx->c[a] * ctx->h * ctx->h / ctx->tau;
+    g->TE[a] = ctx->TE[a];
+    g->TN[a] = ctx->TN[a];
+    g->F[a] = ctx->F[a];
+    for (int b = 0; b < ctx->L; ++b) {
+      g->qconst[a][b] = ctx->sigma[a][b] * ctx->h * ctx->h;
+      g->qcell[a][b] = ctx->qcell[a][b];
+    }
+  }
+}
+
+cudaError_t mc_launch_apply(mc_ctx* ctx, int scheme, double* const* x, double* const* y) {
+  ApplyArgs g{};
+  fill_apply(ctx, &g);
+  g.coupled = scheme == MC_SCHEME_COUPLED;
+  g.rhs = false;
+  for (int a = 0; a < ctx->L; ++a) {
+    g.x[a] = x[a];
+    g.y[a] = y[a];
+  }
+  apply_kernel<<<grid_for(ctx->N), 256, 0, ctx->stream>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t mc_launch_rhs(mc_ctx* ctx, double* const* b) {
+  ApplyArgs g{};
+  fill_apply(ctx, &g);
+  g.rhs = true;
+  for (int a = 0; a < ctx->L; ++a) {
+    g.x[a] = ctx->p[a];
+    g.y[a] = b[a];
+  }
+  apply_kernel<<<grid_for(ctx->N), 256, 0, ctx->stream>>>(g);
+  return cudaGetLastError();
+}
