@@ -32,11 +32,12 @@ def harmonic_face(ka, kb):
     return out
 
 
-def diffusion_matrix(TE, TN, nx, ny):
+def diffusion_matrix(TE, TN, nx, ny, dtype=np.float64):
     """D_alpha: a_ii = sum_n T_in, a_ij = -T_ij (Section 3.1, entries a).
 
     TE[j, i] is the face between (i, j) and (i+1, j); TN[j, i] the face
-    between (i, j) and (i, j+1).
+    between (i, j) and (i, j+1). The diagonal is the sum of the duplicate
+    (i, i) entries, formed in `dtype`.
     """
     N = nx * ny
     idx = np.arange(N).reshape(ny, nx)
@@ -48,9 +49,9 @@ def diffusion_matrix(TE, TN, nx, ny):
         rows += [a, b, a, b]
         cols += [a, b, b, a]
         vals += [t, t, -t, -t]
-    return sp.csr_matrix((np.concatenate(vals),
+    return sp.csr_matrix((np.concatenate(vals).astype(dtype),
                           (np.concatenate(rows), np.concatenate(cols))),
-                         shape=(N, N))
+                         shape=(N, N), dtype=dtype)
 
 
 class FVSystem:
@@ -93,20 +94,28 @@ class FVSystem:
                 out += self.q[(a, b)]
         return out
 
-    def A_block(self, a, b):
-        """Block (a, b) of A = D + Q (Section 3.1, matrix Q)."""
+    def A_block(self, a, b, dtype=np.float64):
+        """Block (a, b) of A = D + Q (Section 3.1, matrix Q), its entries
+        summed in `dtype` (longdouble keeps 1^T D = 0 to extended precision:
+        an FP64 diagonal sum of T breaks it by eps * sum T per row)."""
         if a == b:
-            return (self.D[a] + sp.diags(self.exchange_sum(a))).tocsr()
-        return sp.diags(-self.q[(a, b)]).tocsr()
+            D = self.D[a] if dtype == np.float64 else diffusion_matrix(
+                self.TE[a], self.TN[a], self.nx, self.ny, dtype)
+            ex = np.zeros(self.N, dtype=dtype)
+            for c in range(self.L):
+                if c != a:
+                    ex += self.q[(a, c)].astype(dtype)
+            return (D + sp.diags(ex)).tocsr()
+        return sp.diags(-self.q[(a, b)].astype(dtype)).tocsr()
 
-    def A(self):
+    def A(self, dtype=np.float64):
         """The full coupled operator A = D + Q, continuum-major ordering."""
         L = self.L
-        return sp.bmat([[self.A_block(a, b) for b in range(L)] for a in range(L)],
+        return sp.bmat([[self.A_block(a, b, dtype) for b in range(L)] for a in range(L)],
                        format="csr")
 
-    def M(self):
-        return sp.diags(np.concatenate(self.m)).tocsr()
+    def M(self, dtype=np.float64):
+        return sp.diags(np.concatenate(self.m).astype(dtype)).tocsr()
 
     def apply_A(self, p):
         """A p for a list of L flat state vectors (a plain matrix product)."""

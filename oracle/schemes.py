@@ -13,10 +13,12 @@
 
 Each linear system is factorised once (tau is fixed) with SuperLU and every
 solve gets `refine` sweeps of iterative refinement whose residual b - A x is
-formed in extended precision (numpy longdouble) against the assembled
-matrix. An FP64 residual would leave a forward error of about kappa * eps in
-the near-null constant mode of these Neumann systems (4.5e-11 measured at
-128 x 128 for the k ~ 1e4 continuum); the extended residual removes it. Parity pinned by the closed-form uniform recurrence, the
+formed in extended precision (numpy longdouble), with A assembled in extended
+precision from the FP64 coefficients. The systems have a near-null constant
+mode held only by the mass and exchange terms; an FP64 residual, or an FP64
+sum a_ii = m/tau + sum q + sum T (which breaks 1^T D = 0 by eps * sum T per
+row), shifts that mode by ~1e-11 (128 x 128) to ~1e-10 (1024 x 1024)
+relative. Parity pinned by the closed-form uniform recurrence, the
 cosine-mode decay factor, sigma = 0 reduction, mass and energy identities and
 dense brute force (see the CPU tests).
 """
@@ -37,21 +39,24 @@ class Oracle:
         self._fact = {}
 
     # -- matrices ---------------------------------------------------------
-    def coupled_matrix(self):
+    def coupled_matrix(self, dtype=np.float64):
         """M/tau + D + Q over all continua (Eq. ct-mc)."""
-        return (self.fv.M() / self.tau + self.fv.A()).tocsc()
+        mt = np.concatenate(self.fv.m) / self.tau
+        return (sp.diags(mt.astype(dtype)) + self.fv.A(dtype)).tocsc()
 
-    def split_matrix(self, a):
+    def split_matrix(self, a, dtype=np.float64):
         """M_a/tau + D_a + sum_b Q_ab: the diagonal block of M/tau + A0."""
         fv = self.fv
-        return (sp.diags(fv.m[a] / self.tau) + fv.A_block(a, a)).tocsc()
+        return (sp.diags((fv.m[a] / self.tau).astype(dtype)) + fv.A_block(a, a, dtype)).tocsc()
 
     # -- direct solves ----------------------------------------------------
     def _factor(self, key):
         if key not in self._fact:
-            A = self.coupled_matrix() if key == "coupled" else self.split_matrix(key)
-            Ae = A.astype(np.longdouble).tocsr()
-            self._fact[key] = (Ae, splu(A, permc_spec=self.permc_spec))
+            if key == "coupled":
+                A, Ae = self.coupled_matrix(), self.coupled_matrix(np.longdouble)
+            else:
+                A, Ae = self.split_matrix(key), self.split_matrix(key, np.longdouble)
+            self._fact[key] = (Ae.tocsr(), splu(A, permc_spec=self.permc_spec))
         return self._fact[key]
 
     def solve(self, key, b):
