@@ -13,10 +13,10 @@ contrasts and source structure of the paper's 2C/3C problems.
 
 from .fields import correlated_lognormal, segment_lengths, random_segments
 from .configs import (Workload, dual_64, triple_1024, precision_4096,
-                      batched_instances, nlmc_1024, scaled, by_name)
+                      fracture_instance, batched_instances, nlmc_1024, scaled, by_name)
 
 __all__ = [
     "correlated_lognormal", "segment_lengths", "random_segments", "Workload",
-    "dual_64", "triple_1024", "precision_4096", "batched_instances",
+    "dual_64", "triple_1024", "precision_4096", "fracture_instance", "batched_instances",
     "nlmc_1024", "scaled", "by_name",
 ]

@@ -4,12 +4,38 @@
 #include <math.h>
 #include <string.h>
 
+#include <cudaTypedefs.h>
+
 #include <new>
 #include <string>
 
 #include "mc_internal.h"
 
 namespace {
+
+// Host <-> device copies between dense nx*ny host arrays and pitched fields.
+cudaError_t h2d(const mc_ctx* ctx, double* dst, const double* src) {
+  return cudaMemcpy2DAsync(dst, ctx->pitch * sizeof(double), src, ctx->nx * sizeof(double),
+                           ctx->nx * sizeof(double), ctx->ny, cudaMemcpyHostToDevice, ctx->stream);
+}
+
+cudaError_t d2h(const mc_ctx* ctx, double* dst, const double* src) {
+  return cudaMemcpy2DAsync(dst, ctx->nx * sizeof(double), src, ctx->pitch * sizeof(double),
+                           ctx->nx * sizeof(double), ctx->ny, cudaMemcpyDeviceToHost, ctx->stream);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
 
 thread_local std::string g_setup_err;
 
@@ -61,6 +87,20 @@ mc_status check_opts(const mc_opts* o, std::string* why) {
 
 }  // namespace
 
+cudaError_t mc_encode_map(CUtensorMap* map, CUtensorMapDataType dtype, int esize, void* base, int nx,
+                          int ny, int pitch_elems, int box_x, int box_y) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch_elems * (cuuint64_t)esize};
+  cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, dtype, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t mc_alloc(mc_ctx* ctx, void** ptr, size_t bytes) {
   *ptr = nullptr;
   if (bytes == 0) bytes = 8;
@@ -76,7 +116,9 @@ void mc_fill_params(const mc_ctx* ctx, StepParams* sp, int scheme, int nsteps) {
   sp->nx = ctx->nx;
   sp->ny = ctx->ny;
   sp->L = ctx->L;
+  sp->pitch = ctx->pitch;
   sp->N = ctx->N;
+  sp->Np = ctx->Np;
   sp->scheme = scheme;
   sp->nsteps = nsteps;
   sp->max_iter = ctx->opts.max_iter;
@@ -197,6 +239,8 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
   ctx->ny = g->ny;
   ctx->L = L;
   ctx->N = N;
+  ctx->pitch = mc_pitch_for(g->nx);
+  ctx->Np = (long long)g->ny * ctx->pitch;
   ctx->h = 1.0 / g->nx;
   ctx->tau = tau;
   ctx->opts = o;
@@ -222,7 +266,7 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
   } while (0)
   CKS(cudaGetDevice(&ctx->device));
   CKS(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
-  const size_t fb = (size_t)N * sizeof(double);
+  const size_t fb = (size_t)ctx->Np * sizeof(double);
   // Per-cell exchange arrays (sigma first, scaled to q = sigma h^2 on device).
   if (sigma_cell) {
     int pi = 0;
@@ -231,7 +275,7 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
         if (!sigma_cell[pi]) continue;
         CKS(mc_alloc(ctx, (void**)&ctx->qcell[a][b], fb));
         ctx->qcell[b][a] = ctx->qcell[a][b];
-        CKS(cudaMemcpyAsync(ctx->qcell[a][b], sigma_cell[pi], fb, cudaMemcpyHostToDevice, ctx->stream));
+        CKS(h2d(ctx, ctx->qcell[a][b], sigma_cell[pi]));
       }
   }
   for (int a = 0; a < L; ++a) {
@@ -266,10 +310,22 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
   // Coefficients: k goes through the r buffer (work space, free until the
   // first step) into TE / TN.
   for (int a = 0; a < L; ++a) {
-    CKS(cudaMemcpyAsync(ctx->r[a], k[a], fb, cudaMemcpyHostToDevice, ctx->stream));
+    CKS(h2d(ctx, ctx->r[a], k[a]));
     CKS(mc_launch_setup(ctx, a, ctx->r[a]));
   }
   for (int a = 0; a < L; ++a) CKS(mc_launch_diag(ctx, a));
+  // TMA descriptors of the tiles the stencil phase stages in shared memory.
+  for (int a = 0; a < L; ++a) {
+    const int bx = mc_step_box_x(), by = mc_step_box_y();
+    CKS(mc_encode_map(&ctx->maps.r[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, ctx->r[a], ctx->nx, ctx->ny,
+                      ctx->pitch, bx, by));
+    CKS(mc_encode_map(&ctx->maps.P[0][a], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, ctx->P[0][a], ctx->nx,
+                      ctx->ny, ctx->pitch, bx, by));
+    CKS(mc_encode_map(&ctx->maps.P[1][a], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, ctx->P[1][a], ctx->nx,
+                      ctx->ny, ctx->pitch, bx, by));
+    CKS(mc_encode_map(&ctx->maps.invd[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, ctx->invd[a], ctx->nx,
+                      ctx->ny, ctx->pitch, bx, by));
+  }
   CKS(cudaStreamSynchronize(ctx->stream));
 #undef CKS
   *out = ctx;
@@ -298,7 +354,7 @@ mc_status mc_set_source(mc_ctx* ctx, int32_t alpha, const double* F) {
   for (long long i = 0; i < ctx->N; ++i)
     if (!isfinite(F[i])) return set_err(ctx, MC_E_ARG, "F must be finite");
   CK(cudaSetDevice(ctx->device));
-  CK(cudaMemcpyAsync(ctx->F[alpha], F, ctx->N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(h2d(ctx, ctx->F[alpha], F));
   CK(cudaStreamSynchronize(ctx->stream));
   return MC_OK;
 }
@@ -309,8 +365,7 @@ mc_status mc_set_state(mc_ctx* ctx, const double* const* p) {
   for (int a = 0; a < ctx->L; ++a)
     if (!p[a]) return set_err(ctx, MC_E_ARG, "p[a] is NULL");
   CK(cudaSetDevice(ctx->device));
-  for (int a = 0; a < ctx->L; ++a)
-    CK(cudaMemcpyAsync(ctx->p[a], p[a], ctx->N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  for (int a = 0; a < ctx->L; ++a) CK(h2d(ctx, ctx->p[a], p[a]));
   CK(cudaStreamSynchronize(ctx->stream));
   return MC_OK;
 }
@@ -321,8 +376,7 @@ mc_status mc_get_state(mc_ctx* ctx, double* const* p) {
   for (int a = 0; a < ctx->L; ++a)
     if (!p[a]) return set_err(ctx, MC_E_ARG, "p[a] is NULL");
   CK(cudaSetDevice(ctx->device));
-  for (int a = 0; a < ctx->L; ++a)
-    CK(cudaMemcpyAsync(p[a], ctx->p[a], ctx->N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  for (int a = 0; a < ctx->L; ++a) CK(d2h(ctx, p[a], ctx->p[a]));
   CK(cudaStreamSynchronize(ctx->stream));
   return MC_OK;
 }
@@ -366,7 +420,7 @@ static mc_status run_steps(mc_ctx* ctx, int scheme, int nsteps, mc_stats* stats)
   if (st != MC_OK) {
     // Roll the state back to the start of the failed step.
     for (int a = 0; a < ctx->L; ++a)
-      CK(cudaMemcpyAsync(ctx->p[a], ctx->pprev[a], ctx->N * sizeof(double), cudaMemcpyDeviceToDevice,
+      CK(cudaMemcpyAsync(ctx->p[a], ctx->pprev[a], ctx->Np * sizeof(double), cudaMemcpyDeviceToDevice,
                          ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
   }
@@ -392,10 +446,9 @@ mc_status mc_step_coupled(mc_ctx* ctx, int32_t nsteps, mc_stats* stats) {
 mc_status mc_get_coefficients(mc_ctx* ctx, int32_t alpha, double* TE, double* TN, double* diag) {
   if (!ctx || alpha < 0 || alpha >= ctx->L) return MC_E_ARG;
   CK(cudaSetDevice(ctx->device));
-  const size_t fb = ctx->N * sizeof(double);
-  if (TE) CK(cudaMemcpyAsync(TE, ctx->TE[alpha], fb, cudaMemcpyDeviceToHost, ctx->stream));
-  if (TN) CK(cudaMemcpyAsync(TN, ctx->TN[alpha], fb, cudaMemcpyDeviceToHost, ctx->stream));
-  if (diag) CK(cudaMemcpyAsync(diag, ctx->invd[alpha], fb, cudaMemcpyDeviceToHost, ctx->stream));
+  if (TE) CK(d2h(ctx, TE, ctx->TE[alpha]));
+  if (TN) CK(d2h(ctx, TN, ctx->TN[alpha]));
+  if (diag) CK(d2h(ctx, diag, ctx->invd[alpha]));
   CK(cudaStreamSynchronize(ctx->stream));
   if (diag)
     for (long long i = 0; i < ctx->N; ++i) diag[i] = 1.0 / diag[i];
@@ -407,15 +460,13 @@ mc_status mc_apply(mc_ctx* ctx, int32_t scheme, const double* const* x, double* 
   if (scheme != MC_SCHEME_COUPLED && (scheme < MC_SCHEME_D || scheme > MC_SCHEME_U))
     return set_err(ctx, MC_E_ARG, "bad scheme");
   CK(cudaSetDevice(ctx->device));
-  const size_t fb = ctx->N * sizeof(double);
   // r and q are step work space: free between steps.
   for (int a = 0; a < ctx->L; ++a) {
     if (!x[a] || !y[a]) return set_err(ctx, MC_E_ARG, "x[a] / y[a] NULL");
-    CK(cudaMemcpyAsync(ctx->r[a], x[a], fb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(h2d(ctx, ctx->r[a], x[a]));
   }
   CK(mc_launch_apply(ctx, scheme, ctx->r, ctx->q));
-  for (int a = 0; a < ctx->L; ++a)
-    CK(cudaMemcpyAsync(y[a], ctx->q[a], fb, cudaMemcpyDeviceToHost, ctx->stream));
+  for (int a = 0; a < ctx->L; ++a) CK(d2h(ctx, y[a], ctx->q[a]));
   CK(cudaStreamSynchronize(ctx->stream));
   return MC_OK;
 }
@@ -426,7 +477,7 @@ mc_status mc_rhs_decoupled(mc_ctx* ctx, double* const* b) {
   CK(mc_launch_rhs(ctx, ctx->q));
   for (int a = 0; a < ctx->L; ++a) {
     if (!b[a]) return set_err(ctx, MC_E_ARG, "b[a] NULL");
-    CK(cudaMemcpyAsync(b[a], ctx->q[a], ctx->N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(d2h(ctx, b[a], ctx->q[a]));
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return MC_OK;

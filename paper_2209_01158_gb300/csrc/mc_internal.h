@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libmc.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -12,10 +13,12 @@
 #define MCL MC_MAX_CONTINUA
 
 // Everything the persistent time-stepping kernel needs, passed by value.
-// Field pointers address nx*ny doubles, cell (i, j) at j*nx + i.
+// Field pointers address ny rows of `pitch` doubles, cell (i, j) at
+// j*pitch + i; the pitch is nx rounded up to 16 and the padding stays zero.
 struct StepParams {
-  int nx, ny, L;
-  long long N;
+  int nx, ny, L, pitch;
+  long long N;         // nx * ny
+  long long Np;        // ny * pitch
   int scheme;          // MC_SCHEME_*
   int nsteps;
   int max_iter;
@@ -49,11 +52,19 @@ struct StepParams {
   long long spin_limit;
 };
 
+// TMA descriptors of the arrays the stencil phase reads through tiles.
+struct TmaMaps {
+  CUtensorMap r[MCL];
+  CUtensorMap P[2][MCL];
+  CUtensorMap invd[MCL];
+};
+
 struct mc_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
-  int nx = 0, ny = 0, L = 0;
-  long long N = 0;
+  int nx = 0, ny = 0, L = 0, pitch = 0;
+  long long N = 0, Np = 0;
+  TmaMaps maps;
   double h = 0, tau = 0;
   double c[MCL] = {};
   double sigma[MCL][MCL] = {};
@@ -97,6 +108,15 @@ cudaError_t mc_launch_steps(mc_ctx* ctx, const StepParams& sp, int blocks,
 
 // Maximum co-resident CTAs for the step kernel of this L (cooperative grid).
 int mc_step_max_blocks(int L, int threads, int num_sms);
+int mc_step_box_x();
+int mc_step_box_y();
+
+// Encode a 2-D tiled tensor map (x innermost) over a pitched array.
+cudaError_t mc_encode_map(CUtensorMap* map, CUtensorMapDataType dtype, int esize, void* base,
+                          int nx, int ny, int pitch_elems, int box_x, int box_y);
+
+// Row pitch (elements) used for every device field of an nx-wide grid.
+inline int mc_pitch_for(int nx) { return (nx + 15) / 16 * 16; }
 
 // Setup kernels (mc_setup_kernels.cu).
 cudaError_t mc_launch_setup(mc_ctx* ctx, int a, const double* k_dev);

@@ -1,5 +1,6 @@
 // Coefficient set-up (once per context) and the standalone operator /
-// right-hand-side kernels used to inspect a context.
+// right-hand-side kernels used to inspect a context. Fields are pitched:
+// cell (i, j) at j*pitch + i, padding columns zero and never written.
 //
 // Section 3.1, Eq. app-md: T_ij = k_face |E_ij| / d_ij. Cells are squares, so
 // |E| = d = h and T = k_face; the face value is the harmonic mean of the two
@@ -13,12 +14,13 @@
 
 namespace {
 
-__global__ void faces_kernel(int nx, int ny, const double* __restrict__ k,
+__global__ void faces_kernel(int nx, int ny, int pitch, const double* __restrict__ k,
                              double* __restrict__ TE, double* __restrict__ TN) {
-  const long long N = (long long)nx * ny;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+  const long long Np = (long long)ny * pitch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Np;
        i += (long long)gridDim.x * blockDim.x) {
-    const int gx = (int)(i % nx), gy = (int)(i / nx);
+    const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+    if (gx >= nx) continue;
     const double kc = k[i];
     double te = 0.0, tn = 0.0;
     if (gx + 1 < nx) {
@@ -27,7 +29,7 @@ __global__ void faces_kernel(int nx, int ny, const double* __restrict__ k,
       te = s > 0.0 ? 2.0 * kc * kn / s : 0.0;
     }
     if (gy + 1 < ny) {
-      const double kn = k[i + nx];
+      const double kn = k[i + pitch];
       const double s = kc + kn;
       tn = s > 0.0 ? 2.0 * kc * kn / s : 0.0;
     }
@@ -43,7 +45,7 @@ __global__ void scale_kernel(long long N, double* __restrict__ x, double s) {
 }
 
 struct DiagArgs {
-  int nx, ny, L, a;
+  int nx, ny, pitch, L, a;
   double mtau;
   double qconst[MCL];
   const double* qcell[MCL];
@@ -54,10 +56,11 @@ struct DiagArgs {
 };
 
 __global__ void diag_kernel(DiagArgs g) {
-  const long long N = (long long)g.nx * g.ny;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+  const long long Np = (long long)g.ny * g.pitch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Np;
        i += (long long)gridDim.x * blockDim.x) {
-    const int gx = (int)(i % g.nx), gy = (int)(i / g.nx);
+    const int gy = (int)(i / g.pitch), gx = (int)(i - (long long)gy * g.pitch);
+    if (gx >= g.nx) continue;
     double dc = g.mtau;
     for (int b = 0; b < g.L; ++b) {
       if (b == g.a) continue;
@@ -65,14 +68,14 @@ __global__ void diag_kernel(DiagArgs g) {
     }
     double t = g.TE[i] + g.TN[i];
     if (gx > 0) t += g.TE[i - 1];
-    if (gy > 0) t += g.TN[i - g.nx];
+    if (gy > 0) t += g.TN[i - g.pitch];
     if (g.diagc) g.diagc[i] = dc;
     g.invd[i] = 1.0 / (dc + t);
   }
 }
 
 struct ApplyArgs {
-  int nx, ny, L;
+  int nx, ny, pitch, L;
   bool coupled;
   double mtau[MCL];
   double qconst[MCL][MCL];
@@ -90,11 +93,12 @@ __device__ __forceinline__ double q_of(const ApplyArgs& g, int a, int b, long lo
 }
 
 __global__ void apply_kernel(ApplyArgs g) {
-  const long long N = (long long)g.nx * g.ny;
-  const int nx = g.nx;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+  const long long Np = (long long)g.ny * g.pitch;
+  const int nx = g.nx, pitch = g.pitch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Np;
        i += (long long)gridDim.x * blockDim.x) {
-    const int gx = (int)(i % nx), gy = (int)(i / nx);
+    const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+    if (gx >= nx) continue;
     for (int a = 0; a < g.L; ++a) {
       const double xc = g.x[a][i];
       double v;
@@ -106,8 +110,8 @@ __global__ void apply_kernel(ApplyArgs g) {
         v = g.mtau[a] * xc;
         if (gx + 1 < nx) v += g.TE[a][i] * (xc - g.x[a][i + 1]);
         if (gx > 0) v += g.TE[a][i - 1] * (xc - g.x[a][i - 1]);
-        if (gy + 1 < g.ny) v += g.TN[a][i] * (xc - g.x[a][i + nx]);
-        if (gy > 0) v += g.TN[a][i - nx] * (xc - g.x[a][i - nx]);
+        if (gy + 1 < g.ny) v += g.TN[a][i] * (xc - g.x[a][i + pitch]);
+        if (gy > 0) v += g.TN[a][i - pitch] * (xc - g.x[a][i - pitch]);
         for (int b = 0; b < g.L; ++b) {
           if (b == a) continue;
           const double qv = q_of(g, a, b, i);
@@ -130,9 +134,10 @@ int grid_for(long long N) {
 }  // namespace
 
 cudaError_t mc_launch_setup(mc_ctx* ctx, int a, const double* k_dev) {
-  const long long N = ctx->N;
+  const long long N = ctx->Np;
   const int blocks = grid_for(N);
-  faces_kernel<<<blocks, 256, 0, ctx->stream>>>(ctx->nx, ctx->ny, k_dev, ctx->TE[a], ctx->TN[a]);
+  faces_kernel<<<blocks, 256, 0, ctx->stream>>>(ctx->nx, ctx->ny, ctx->pitch, k_dev, ctx->TE[a],
+                                                ctx->TN[a]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // Per-cell exchange arrays hold sigma on upload; scale them to q = sigma h^2
@@ -150,6 +155,7 @@ cudaError_t mc_launch_diag(mc_ctx* ctx, int a) {
   DiagArgs g{};
   g.nx = ctx->nx;
   g.ny = ctx->ny;
+  g.pitch = ctx->pitch;
   g.L = ctx->L;
   g.a = a;
   g.mtau = ctx->c[a] * ctx->h * ctx->h / ctx->tau;
@@ -161,13 +167,14 @@ cudaError_t mc_launch_diag(mc_ctx* ctx, int a) {
   g.TN = ctx->TN[a];
   g.diagc = ctx->diagc[a];
   g.invd = ctx->invd[a];
-  diag_kernel<<<grid_for(ctx->N), 256, 0, ctx->stream>>>(g);
+  diag_kernel<<<grid_for(ctx->Np), 256, 0, ctx->stream>>>(g);
   return cudaGetLastError();
 }
 
 static void fill_apply(const mc_ctx* ctx, ApplyArgs* g) {
   g->nx = ctx->nx;
   g->ny = ctx->ny;
+  g->pitch = ctx->pitch;
   g->L = ctx->L;
   for (int a = 0; a < ctx->L; ++a) {
     g->mtau[a] = ctx->c[a] * ctx->h * ctx->h / ctx->tau;
@@ -190,7 +197,7 @@ cudaError_t mc_launch_apply(mc_ctx* ctx, int scheme, double* const* x, double* c
     g.x[a] = x[a];
     g.y[a] = y[a];
   }
-  apply_kernel<<<grid_for(ctx->N), 256, 0, ctx->stream>>>(g);
+  apply_kernel<<<grid_for(ctx->Np), 256, 0, ctx->stream>>>(g);
   return cudaGetLastError();
 }
 
@@ -202,6 +209,6 @@ cudaError_t mc_launch_rhs(mc_ctx* ctx, double* const* b) {
     g.x[a] = ctx->p[a];
     g.y[a] = b[a];
   }
-  apply_kernel<<<grid_for(ctx->N), 256, 0, ctx->stream>>>(g);
+  apply_kernel<<<grid_for(ctx->Np), 256, 0, ctx->stream>>>(g);
   return cudaGetLastError();
 }

@@ -8,27 +8,47 @@
 //                                        + sum_b Q_ab p_b^{n-1 or n},
 // the coupled scheme (M/tau + D + Q) p^n = M/tau p^{n-1} + F.
 //
-// Layout: every field is nx*ny doubles, cell (i, j) at j*nx + i. TE holds the
-// east-face transmissibility (0 on the last column), TN the north face (0 on
-// the last row). The PCG warm-starts from p^{n-1} and updates p in place.
+// Layout: every field is ny rows of `pitch` doubles (pitch = nx rounded up to
+// 16, padding zero), cell (i, j) at j*pitch + i. TE holds the east-face
+// transmissibility (0 on the last column), TN the north face (0 on the last
+// row). The PCG warm-starts from p^{n-1} and updates p in place.
 //
-// Cross-CTA data written inside the launch (r, P, q, p, partial sums) is read
-// with ld.global.cg so no SM serves it from a stale L1 line; read-only
-// coefficients go through the read-only path. Reductions are deterministic:
-// warp butterflies, then a fixed-order sum over warps and over CTAs.
+// PCG iteration = two phases separated by grid barriers:
+//   A (stencil): per 64 x 8 tile, TMA brings the halo boxes of r, P_old and
+//     invd into shared memory (a ring of up to 6 stages: the next tiles'
+//     boxes load while this one computes); P_new = invd*r + beta*P_old on the 66 x 10
+//     halo region, then q = A P_new on the tile and <P_new, q>.
+//   B (pointwise, vectorised): x += alpha P_new, r -= alpha q, <r, r>,
+//     <r, invd r>.
+// Cross-CTA data written inside the launch is read through L2 (ld.cg or TMA,
+// after a proxy fence); read-only coefficients use the read-only path.
+// Reductions are deterministic: warp butterflies, then fixed-order sums over
+// warps and over CTAs.
 
 #include <math.h>
 
 #include "mc_internal.h"
+#include "mc_tma.h"
 
 namespace {
 
-constexpr int TX = 64;   // stencil tile width (cells along x)
-constexpr int TY = 8;    // stencil tile height
-constexpr int HX = TX + 2;
-constexpr int HY = TY + 2;
-constexpr int NT = 512;  // threads per CTA (launch bound)
-constexpr int KMAX = 4 * MCL;  // partial-sum quantities per slot
+constexpr int TX = 64;          // stencil tile width (cells along x)
+constexpr int TY = 8;           // stencil tile height
+constexpr int HOFF = 2;         // box starts 2 doubles (16 B) left of the tile
+constexpr int BX = TX + 2 * HOFF;   // 68: box width (doubles), 544 B rows
+constexpr int BY = TY + 2;          // 10: box height
+constexpr int ABOX = 688;       // box slot in doubles (5504 B, 128-B multiple)
+constexpr uint32_t BOX_BYTES = BX * BY * 8;
+constexpr int PX = TX + 2;      // 66: P_new halo region width
+constexpr int PN = PX * BY;     // 660 cells
+constexpr int NT = 512;         // threads per CTA
+constexpr int KMAX = 4 * MCL;   // partial-sum quantities per slot
+
+// TMA pipeline depth: enough boxes in flight per SM to cover the DRAM
+// latency (Little's law: ~64 KB per SM), within 227 KB of shared memory.
+__host__ __device__ constexpr int nstage(int L, bool coupled) {
+  return !coupled ? 6 : (L <= 1 ? 6 : (L == 2 ? 4 : 3));
+}
 
 __device__ __forceinline__ double ldc(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ double ldr(const double* p) { return __ldg(p); }
@@ -43,6 +63,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+__device__ __forceinline__ void raise_abort(const StepParams& sp, int code) {
+  atomicExch(sp.bar_gen + 32, 1u);
+  atomicCAS(sp.status, 0, code);
 }
 
 // Grid-wide barrier for a cooperative launch. Every wait is bounded by
@@ -68,8 +93,7 @@ __device__ bool grid_sync(const StepParams& sp) {
       while (ld_acquire(gen) == g) {
         if (ld_acquire(abort_word) != 0u) { ok = 0; break; }
         if (++n > sp.spin_limit) {
-          atomicExch(abort_word, 1u);
-          atomicCAS(sp.status, 0, (int)MC_E_TIMEOUT);
+          raise_abort(sp, (int)MC_E_TIMEOUT);
           ok = 0;
           break;
         }
@@ -78,15 +102,15 @@ __device__ bool grid_sync(const StepParams& sp) {
     }
     __threadfence();
     if (ok && ld_acquire(abort_word) != 0u) ok = 0;
+    // Other CTAs' generic stores are now visible; order them before this
+    // thread's later TMA reads.
+    fence_proxy_async();
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
 }
 
-// Block-reduce NQ values and store them as this CTA's partials:
-// partials[slot][k][blockIdx.x], KMAX quantities reserved per slot so the
-// two alternating slots never overlap whatever NQ each phase uses.
 template <int NQ>
 __device__ void block_store(double (&v)[NQ], double* s_red, double* partials, int slot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -105,7 +129,6 @@ __device__ void block_store(double (&v)[NQ], double* s_red, double* partials, in
   __syncthreads();
 }
 
-// Sum the NQ partials over all CTAs in a fixed order; every thread gets them.
 template <int NQ>
 __device__ void grid_sum(const double* partials, int slot, double* s_res, double (&out)[NQ]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -138,27 +161,37 @@ __device__ __forceinline__ double diagc(const StepParams& sp, int a, long long i
 // D_a x at cell (gx, gy): sum over faces of T (x_i - x_neighbour).
 __device__ __forceinline__ double stencil_flux(const StepParams& sp, int a, const double* x,
                                                int gx, int gy, long long i, double xc) {
-  const int nx = sp.nx;
+  const int pitch = sp.pitch;
   double s = 0.0;
-  const double te = ldr(sp.TE[a] + i);
-  const double tn = ldr(sp.TN[a] + i);
-  if (gx + 1 < nx) s += te * (xc - ldc(x + i + 1));
+  if (gx + 1 < sp.nx) s += ldr(sp.TE[a] + i) * (xc - ldc(x + i + 1));
   if (gx > 0) s += ldr(sp.TE[a] + i - 1) * (xc - ldc(x + i - 1));
-  if (gy + 1 < sp.ny) s += tn * (xc - ldc(x + i + nx));
-  if (gy > 0) s += ldr(sp.TN[a] + i - nx) * (xc - ldc(x + i - nx));
+  if (gy + 1 < sp.ny) s += ldr(sp.TN[a] + i) * (xc - ldc(x + i + pitch));
+  if (gy > 0) s += ldr(sp.TN[a] + i - pitch) * (xc - ldc(x + i - pitch));
   return s;
 }
+
+struct Smem {
+  double* box;      // [NST stages][NARR][ABOX]
+  double* pn;       // [NL][PN]
+  double* red;      // [NT/32][KMAX]
+  double* res;      // [KMAX]
+  uint64_t* bar;    // [NST]
+};
 
 // ---------------------------------------------------------------------------
 // One linear solve: the continua in `mask` (decoupled, independent systems),
 // or all L continua as one coupled system. Warm start from p, result in p.
 // Returns false when the run must stop (timeout, breakdown, no convergence).
 template <int L, bool COUPLED>
-__device__ bool pcg_solve(const StepParams& sp, unsigned mask, double* s_tile,
-                          double* s_red, double* s_res) {
-  const long long N = sp.N;
-  const int nx = sp.nx;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned mask, Smem& sm,
+                          uint32_t& phb) {
+  constexpr int NL = COUPLED ? L : 1;
+  constexpr int NARR = 3 * NL;
+  constexpr int NST = nstage(L, COUPLED);
+  const int nx = sp.nx, ny = sp.ny, pitch = sp.pitch;
+  const long long Np = sp.Np;
+  const int tid = threadIdx.x;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
   const long long gstride = (long long)gridDim.x * blockDim.x;
 
   // ---- fused right-hand side + initial residual (slot 0: bb, rr, rz) -----
@@ -169,8 +202,9 @@ __device__ bool pcg_solve(const StepParams& sp, unsigned mask, double* s_tile,
   for (int a = 0; a < L; ++a) {
     if (!(mask & (1u << a))) continue;
     const double* pa = sp.p[a];
-    for (long long i = gtid; i < N; i += gstride) {
-      const int gx = (int)(i % nx), gy = (int)(i / nx);
+    for (long long i = gtid; i < Np; i += gstride) {
+      const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+      if (gx >= nx) continue;
       const double xc = ldc(pa + i);
       const double f = ldr(sp.F[a] + i);
       double ex = 0.0, exb = 0.0;
@@ -192,10 +226,10 @@ __device__ bool pcg_solve(const StepParams& sp, unsigned mask, double* s_tile,
       acc[2 * L + a] += rv * z;
     }
   }
-  block_store<3 * L>(acc, s_red, sp.partials, 0);
+  block_store<3 * L>(acc, sm.red, sp.partials, 0);
   if (!grid_sync(sp)) return false;
   double tot[3 * L];
-  grid_sum<3 * L>(sp.partials, 0, s_res, tot);
+  grid_sum<3 * L>(sp.partials, 0, sm.res, tot);
 
   double bb[L], rr[L], rz[L], beta[L];
 #pragma unroll
@@ -229,13 +263,14 @@ __device__ bool pcg_solve(const StepParams& sp, unsigned mask, double* s_tile,
   for (int a = 0; a < L; ++a) my_iters[a] = 0;
 
   const int tiles = sp.tiles_x * sp.tiles_y;
+  const int lx = tid % TX, ly = tid / TX;  // own cell in the tile (NT == TX * TY)
   while (active) {
     if (it >= sp.max_iter) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(sp.status, 0, (int)MC_E_NOCONV);
+      if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_NOCONV);
       ok = false;
       break;
     }
-    // ---- phase A: P_new = z + beta P_old on a halo tile, q = A P_new ------
+    // ---- phase A: TMA halo tiles, P_new = z + beta P_old, q = A P_new -----
     int act_list[L];
     int nact = 0;
 #pragma unroll
@@ -244,7 +279,9 @@ __device__ bool pcg_solve(const StepParams& sp, unsigned mask, double* s_tile,
 #pragma unroll
     for (int a = 0; a < L; ++a) pq[a] = 0.0;
     const int ntask = COUPLED ? tiles : nact * tiles;
-    for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+
+    // issue the TMA boxes of task t into stage s (thread 0 only)
+    auto issue = [&](int t, int s) {
       int a0 = 0, tt = t;
       if (!COUPLED) {
         const int w = t / tiles;
@@ -252,65 +289,132 @@ __device__ bool pcg_solve(const StepParams& sp, unsigned mask, double* s_tile,
 #pragma unroll
         for (int k = 0; k < L; ++k) if (k == w) a0 = act_list[k];
       }
-      const int x0 = (tt % sp.tiles_x) * TX;
-      const int y0 = (tt / sp.tiles_x) * TY;
-      constexpr int NL = COUPLED ? L : 1;
+      const int bx0 = (tt % sp.tiles_x) * TX - HOFF;
+      const int by0 = (tt / sp.tiles_x) * TY - 1;
+      uint64_t* bar = sm.bar + s;
+      fence_proxy_async();
+      mbar_expect_tx(bar, NARR * BOX_BYTES);
+      double* base = sm.box + (size_t)s * NARR * ABOX;
 #pragma unroll
       for (int l = 0; l < NL; ++l) {
         const int a = COUPLED ? l : a0;
-        const double* r = sp.r[a];
-        const double* Po = sp.P[cur][a];
-        const double* iv = sp.invd[a];
+        tma_load_2d(base + (3 * l + 0) * ABOX, &maps.r[a], bx0, by0, bar);
+        tma_load_2d(base + (3 * l + 1) * ABOX, &maps.P[cur][a], bx0, by0, bar);
+        tma_load_2d(base + (3 * l + 2) * ABOX, &maps.invd[a], bx0, by0, bar);
+      }
+    };
+
+    const int G = gridDim.x;
+    int t = blockIdx.x;
+    int k = 0;
+    unsigned pend = 0;  // stages with a TMA load in flight (uniform in the CTA)
+    // prologue: the first NST-1 tasks of this CTA in flight
+#pragma unroll
+    for (int j = 0; j < NST - 1; ++j) {
+      const int tj = t + j * G;
+      if (tj < ntask) {
+        if (tid == 0) issue(tj, j);
+        pend |= 1u << j;
+      }
+    }
+    bool tma_ok = true;
+    for (; t < ntask; t += G, ++k) {
+      const int s = k % NST;
+      {
+        // refill the stage freed by the previous task with the task NST-1 ahead
+        const int tn = t + (NST - 1) * G;
+        const int sn = (k + NST - 1) % NST;
+        if (tn < ntask) {
+          if (tid == 0) issue(tn, sn);
+          pend |= 1u << sn;
+        }
+      }
+      int a0 = 0, tt = t;
+      if (!COUPLED) {
+        const int w = t / tiles;
+        tt = t - w * tiles;
+#pragma unroll
+        for (int kk = 0; kk < L; ++kk) if (kk == w) a0 = act_list[kk];
+      }
+      const int x0 = (tt % sp.tiles_x) * TX;
+      const int y0 = (tt / sp.tiles_x) * TY;
+      const int gx = x0 + lx, gy = y0 + ly;
+      const bool inside = gx < nx && gy < ny;
+      const long long i = (long long)gy * pitch + gx;
+      // read-only coefficients of the own cell, fetched while TMA lands
+      double te[NL], tw[NL], tn[NL], ts[NL], dc[NL];
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        const int a = COUPLED ? l : a0;
+        te[l] = tw[l] = tn[l] = ts[l] = dc[l] = 0.0;
+        if (inside) {
+          te[l] = ldr(sp.TE[a] + i);
+          tn[l] = ldr(sp.TN[a] + i);
+          if (gx > 0) tw[l] = ldr(sp.TE[a] + i - 1);
+          if (gy > 0) ts[l] = ldr(sp.TN[a] + i - pitch);
+          dc[l] = diagc(sp, a, i);
+        }
+      }
+      if (!mbar_wait(sm.bar + s, (phb >> s) & 1u, sp.spin_limit)) {
+        if (tid == 0) raise_abort(sp, (int)MC_E_TIMEOUT);
+        tma_ok = false;
+        break;
+      }
+      phb ^= 1u << s;
+      pend &= ~(1u << s);
+      const double* base = sm.box + (size_t)s * NARR * ABOX;
+      // P_new on the 66 x 10 halo region (box columns 1..66)
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        const int a = COUPLED ? l : a0;
         const double bt = beta[a];
-        double* st = s_tile + l * HX * HY;
-        for (int e = threadIdx.x; e < HX * HY; e += blockDim.x) {
-          const int ly = e / HX, lx = e - ly * HX;
-          const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-          double v = 0.0;
-          if (gx >= 0 && gx < nx && gy >= 0 && gy < sp.ny) {
-            const long long i = (long long)gy * nx + gx;
-            v = ldr(iv + i) * ldc(r + i) + bt * ldc(Po + i);
-          }
-          st[e] = v;
+        const double* br = base + (3 * l + 0) * ABOX;
+        const double* bp = base + (3 * l + 1) * ABOX;
+        const double* bi = base + (3 * l + 2) * ABOX;
+        double* pn = sm.pn + l * PN;
+        for (int e = tid; e < PN; e += NT) {
+          const int ry = e / PX, rx = e - ry * PX;
+          const int bidx = ry * BX + rx + 1;
+          pn[e] = bi[bidx] * br[bidx] + bt * bp[bidx];
         }
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < TX * TY; e += blockDim.x) {
-        const int ly = e / TX, lx = e - ly * TX;
-        const int gx = x0 + lx, gy = y0 + ly;
-        if (gx >= nx || gy >= sp.ny) continue;
-        const long long i = (long long)gy * nx + gx;
-        const int c = (ly + 1) * HX + lx + 1;
+      if (inside) {
+        const int c = (ly + 1) * PX + lx + 1;
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
           const int a = COUPLED ? l : a0;
-          const double* st = s_tile + l * HX * HY;
-          const double pc = st[c];
-          const double te = ldr(sp.TE[a] + i);
-          const double tn = ldr(sp.TN[a] + i);
-          const double tw = gx > 0 ? ldr(sp.TE[a] + i - 1) : 0.0;
-          const double ts = gy > 0 ? ldr(sp.TN[a] + i - nx) : 0.0;
-          double qv = diagc(sp, a, i) * pc + te * (pc - st[c + 1]) + tw * (pc - st[c - 1]) +
-                      tn * (pc - st[c + HX]) + ts * (pc - st[c - HX]);
+          const double* pn = sm.pn + l * PN;
+          const double pc = pn[c];
+          double qv = dc[l] * pc + te[l] * (pc - pn[c + 1]) + tw[l] * (pc - pn[c - 1]) +
+                      tn[l] * (pc - pn[c + PX]) + ts[l] * (pc - pn[c - PX]);
           if (COUPLED) {
 #pragma unroll
             for (int b = 0; b < L; ++b) {
               if (b == a) continue;
-              qv -= qab(sp, a, b, i) * s_tile[b * HX * HY + c];
+              qv -= qab(sp, a, b, i) * sm.pn[b * PN + c];
             }
           }
           sp.P[cur ^ 1][a][i] = pc;
           sp.q[a][i] = qv;
 #pragma unroll
-          for (int k = 0; k < L; ++k) if (k == a) pq[k] += pc * qv;
+          for (int kk = 0; kk < L; ++kk) if (kk == a) pq[kk] += pc * qv;
         }
       }
       __syncthreads();
     }
-    block_store<L>(pq, s_red, sp.partials, slot);
+    if (!tma_ok) {
+      // Leave no TMA copy landing in this CTA's shared memory after it exits:
+      // wait (bounded again) for every load still in flight.
+      for (int st = 0; st < NST; ++st)
+        if (pend & (1u << st)) mbar_wait(sm.bar + st, (phb >> st) & 1u, 1LL << 24);
+      ok = false;
+      break;
+    }
+    block_store<L>(pq, sm.red, sp.partials, slot);
     if (!grid_sync(sp)) { ok = false; break; }
     double pqt[L];
-    grid_sum<L>(sp.partials, slot, s_res, pqt);
+    grid_sum<L>(sp.partials, slot, sm.res, pqt);
     slot ^= 1;
     if (COUPLED) {
       double s = 0;
@@ -330,35 +434,46 @@ __device__ bool pcg_solve(const StepParams& sp, unsigned mask, double* s_tile,
       }
     }
     if (brk) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(sp.status, 0, (int)MC_E_BREAKDOWN);
+      if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_BREAKDOWN);
       ok = false;
       break;
     }
-    // ---- phase B: x += alpha P, r -= alpha q, z = invd r (slot: rr, rz) ----
+    // ---- phase B: x += alpha P, r -= alpha q (slot: rr, rz), 2 cells/thread --
     double acc2[2 * L];
 #pragma unroll
-    for (int k = 0; k < 2 * L; ++k) acc2[k] = 0.0;
+    for (int kk = 0; kk < 2 * L; ++kk) acc2[kk] = 0.0;
+    const long long Np2 = Np >> 1;
 #pragma unroll
     for (int a = 0; a < L; ++a) {
       if (!(active & (1u << a))) continue;
       const double al = alpha[a];
-      double* x = sp.p[a];
-      double* r = sp.r[a];
-      const double* Pn = sp.P[cur ^ 1][a];
-      const double* qq = sp.q[a];
-      const double* iv = sp.invd[a];
-      for (long long i = gtid; i < N; i += gstride) {
-        const double rv = ldc(r + i) - al * ldc(qq + i);
-        x[i] = ldc(x + i) + al * ldc(Pn + i);
-        r[i] = rv;
-        acc2[a] += rv * rv;
-        acc2[L + a] += rv * (ldr(iv + i) * rv);
+      double2* x = reinterpret_cast<double2*>(sp.p[a]);
+      double2* r = reinterpret_cast<double2*>(sp.r[a]);
+      const double2* Pn = reinterpret_cast<const double2*>(sp.P[cur ^ 1][a]);
+      const double2* qq = reinterpret_cast<const double2*>(sp.q[a]);
+      const double2* iv = reinterpret_cast<const double2*>(sp.invd[a]);
+#pragma unroll 2
+      for (long long j = gtid; j < Np2; j += gstride) {
+        const double2 rv0 = __ldcg(r + j);
+        const double2 qv = __ldcg(qq + j);
+        const double2 xv = __ldcg(x + j);
+        const double2 pv = __ldcg(Pn + j);
+        const double2 dv = __ldg(iv + j);
+        double2 rv, xn;
+        rv.x = rv0.x - al * qv.x;
+        rv.y = rv0.y - al * qv.y;
+        xn.x = xv.x + al * pv.x;
+        xn.y = xv.y + al * pv.y;
+        x[j] = xn;
+        r[j] = rv;
+        acc2[a] += rv.x * rv.x + rv.y * rv.y;
+        acc2[L + a] += rv.x * (dv.x * rv.x) + rv.y * (dv.y * rv.y);
       }
     }
-    block_store<2 * L>(acc2, s_red, sp.partials, slot);
+    block_store<2 * L>(acc2, sm.red, sp.partials, slot);
     if (!grid_sync(sp)) { ok = false; break; }
     double t2[2 * L];
-    grid_sum<2 * L>(sp.partials, slot, s_res, t2);
+    grid_sum<2 * L>(sp.partials, slot, sm.res, t2);
     slot ^= 1;
     if (COUPLED) {
       double s0 = 0, s1 = 0;
@@ -378,36 +493,163 @@ __device__ bool pcg_solve(const StepParams& sp, unsigned mask, double* s_tile,
       my_iters[a] = it;
       if (!(rr[a] > rtol2 * bb[a])) active &= ~(1u << a);
       if (!isfinite(rr[a])) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(sp.status, 0, (int)MC_E_BREAKDOWN);
+        if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_BREAKDOWN);
         ok = false;
       }
     }
     if (!ok) break;
     cur ^= 1;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  // ---- constant-mode correction --------------------------------------------
+  // The zero-flux systems have near-null modes that only the mass and
+  // exchange diagonal holds: the constant of each solved continuum. Because
+  // 1^T D = 0, the exact solution satisfies, for every such constant 1_a,
+  //   1_a^T (b - A x) = sum_i (F + m_a/tau (p_a^{n-1} - x_a) + exchange)_i = 0.
+  // Rounding in A P leaves a residual in these directions that the small
+  // diagonal amplifies; a Galerkin correction x += sum_a c_a 1_a with
+  // G c = 1^T (b - A x), G_ab = 1_a^T A 1_b, restores the identities
+  // (decoupled: one independent 1 x 1 system per continuum; coupled: L x L).
+  // The per-cell terms are differences of nearby values, so the sums are
+  // accurate.
+  if (ok) {
+    constexpr int NPAIR = L * (L - 1) / 2;
+    constexpr int NQC = COUPLED ? L + NPAIR : 2 * L;
+    double cs[NQC];
+#pragma unroll
+    for (int kk = 0; kk < NQC; ++kk) cs[kk] = 0.0;
+    const bool lag_prev = sp.scheme == MC_SCHEME_D;
+    for (long long i = gtid; i < Np; i += gstride) {
+      const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+      if (gx >= nx) continue;
+      double xv[L];
+#pragma unroll
+      for (int a = 0; a < L; ++a) xv[a] = (mask & (1u << a)) ? ldc(sp.p[a] + i) : 0.0;
+      int pi = 0;
+#pragma unroll
+      for (int a = 0; a < L; ++a) {
+        if (!(mask & (1u << a))) continue;
+        double tv = ldr(sp.F[a] + i) + sp.mtau[a] * (ldc(sp.pprev[a] + i) - xv[a]);
+#pragma unroll
+        for (int b = 0; b < L; ++b) {
+          if (b == a) continue;
+          const double pb = COUPLED ? xv[b] : (lag_prev ? ldc(sp.pprev[b] + i) : ldc(sp.p[b] + i));
+          tv += qab(sp, a, b, i) * (pb - xv[a]);
+        }
+        cs[a] += tv;
+        if (!COUPLED) cs[L + a] += diagc(sp, a, i);
+      }
+      if (COUPLED) {
+#pragma unroll
+        for (int a = 0; a < L; ++a)
+#pragma unroll
+          for (int b = a + 1; b < L; ++b) cs[L + pi++] += qab(sp, a, b, i);
+      }
+    }
+    block_store<NQC>(cs, sm.red, sp.partials, slot);
+    if (!grid_sync(sp)) {
+      ok = false;
+    } else {
+      double ct[NQC];
+      grid_sum<NQC>(sp.partials, slot, sm.res, ct);
+      slot ^= 1;
+      double shift[L];
+      if (COUPLED) {
+        // G_aa = N m_a/tau + sum_b Q_ab, G_ab = -Q_ab (Q summed over cells)
+        double G[L][L], c[L];
+#pragma unroll
+        for (int a = 0; a < L; ++a) {
+#pragma unroll
+          for (int b = 0; b < L; ++b) G[a][b] = 0.0;
+          G[a][a] = (double)sp.N * sp.mtau[a];
+          c[a] = ct[a];
+        }
+        int pi = 0;
+#pragma unroll
+        for (int a = 0; a < L; ++a)
+#pragma unroll
+          for (int b = a + 1; b < L; ++b) {
+            const double Q = ct[L + pi++];
+            G[a][a] += Q;
+            G[b][b] += Q;
+            G[a][b] -= Q;
+            G[b][a] -= Q;
+          }
+        // Gaussian elimination (G is SPD: no pivoting needed)
+#pragma unroll
+        for (int kk = 0; kk < L; ++kk) {
+#pragma unroll
+          for (int r = kk + 1; r < L; ++r) {
+            const double f = G[r][kk] / G[kk][kk];
+#pragma unroll
+            for (int cc = kk; cc < L; ++cc) G[r][cc] -= f * G[kk][cc];
+            c[r] -= f * c[kk];
+          }
+        }
+#pragma unroll
+        for (int r = L - 1; r >= 0; --r) {
+          double v = c[r];
+#pragma unroll
+          for (int cc = r + 1; cc < L; ++cc) v -= G[r][cc] * shift[cc];
+          shift[r] = v / G[r][r];
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < L; ++a) shift[a] = ct[L + a] > 0.0 ? ct[a] / ct[L + a] : 0.0;
+      }
+#pragma unroll
+      for (int a = 0; a < L; ++a) {
+        if (!(mask & (1u << a))) continue;
+        const double sh = shift[a];
+        if (!isfinite(sh)) continue;
+        for (long long i = gtid; i < Np; i += gstride) {
+          const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+          if (gx >= nx) continue;
+          sp.p[a][i] = ldc(sp.p[a] + i) + sh;
+        }
+      }
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) {
 #pragma unroll
     for (int a = 0; a < L; ++a) {
       if (!(mask & (1u << a))) continue;
-      const int ka = COUPLED ? 0 : a;
       if (COUPLED && a != 0) continue;
+      const int ka = COUPLED ? 0 : a;
       sp.iters[ka] += my_iters[a];
       if (my_iters[a] > sp.max_iters[ka]) sp.max_iters[ka] = my_iters[a];
       sp.relres[ka] = bb[a] > 0 ? sqrt(rr[a] / bb[a]) : sqrt(rr[a]);
     }
   }
-  // The next solve reads p of this one's continua: make p visible to all.
+  // The next solve's first pass reads p and rewrites partial slot 0: every
+  // CTA must be past this solve's last reads first.
   if (ok && !grid_sync(sp)) ok = false;
   return ok;
 }
 
 template <int L, bool COUPLED>
-__global__ void __launch_bounds__(NT, 1) step_kernel(StepParams sp) {
+__global__ void __launch_bounds__(NT, 1)
+    step_kernel(const __grid_constant__ StepParams sp, const __grid_constant__ TmaMaps maps) {
   constexpr int NL = COUPLED ? L : 1;
-  __shared__ double s_tile[NL * HX * HY];
-  __shared__ double s_red[(NT / 32) * KMAX];
-  __shared__ double s_res[KMAX];
-  const long long N = sp.N;
+  constexpr int NARR = 3 * NL;
+  constexpr int NST = nstage(L, COUPLED);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // TMA destinations need 128-B aligned slots: align the dynamic base.
+  unsigned char* smem_base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  Smem sm;
+  sm.box = reinterpret_cast<double*>(smem_base);
+  sm.pn = sm.box + NST * NARR * ABOX;
+  sm.red = sm.pn + NL * PN;
+  sm.res = sm.red + (NT / 32) * KMAX;
+  sm.bar = reinterpret_cast<uint64_t*>(sm.res + KMAX);
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < NST; ++st) mbar_init(sm.bar + st, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phb = 0u;  // parity of the next completion of each stage
+
+  const long long Np = sp.Np;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gstride = (long long)gridDim.x * blockDim.x;
 
@@ -415,15 +657,15 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepParams sp) {
   bool ok = true;
   for (int step = 0; step < sp.nsteps && ok; ++step) {
     for (int a = 0; a < L; ++a)
-      for (long long i = gtid; i < N; i += gstride) sp.pprev[a][i] = ldc(sp.p[a] + i);
+      for (long long i = gtid; i < Np; i += gstride) sp.pprev[a][i] = ldc(sp.p[a] + i);
     if (COUPLED) {
-      ok = pcg_solve<L, true>(sp, (1u << L) - 1u, s_tile, s_red, s_res);
+      ok = pcg_solve<L, true>(sp, maps, (1u << L) - 1u, sm, phb);
     } else if (sp.scheme == MC_SCHEME_D) {
-      ok = pcg_solve<L, false>(sp, (1u << L) - 1u, s_tile, s_red, s_res);
+      ok = pcg_solve<L, false>(sp, maps, (1u << L) - 1u, sm, phb);
     } else {
       for (int k = 0; k < L && ok; ++k) {
         const int a = sp.scheme == MC_SCHEME_U ? L - 1 - k : k;
-        ok = pcg_solve<L, false>(sp, 1u << a, s_tile, s_red, s_res);
+        ok = pcg_solve<L, false>(sp, maps, 1u << a, sm, phb);
       }
     }
     if (ok) ++done;
@@ -437,7 +679,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepParams sp) {
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const double wa = (!COUPLED && (sp.scheme == MC_SCHEME_D || sp.scheme == MC_SCHEME_U)) ? 1.0 : 0.0;
   const double wb = (!COUPLED && (sp.scheme == MC_SCHEME_D || sp.scheme == MC_SCHEME_L)) ? 1.0 : 0.0;
-  for (long long i = gtid; i < N; i += gstride) {
+  for (long long i = gtid; i < Np; i += gstride) {
     double dp[L];
 #pragma unroll
     for (int a = 0; a < L; ++a) {
@@ -457,10 +699,10 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepParams sp) {
         acc[3] += sp.tau * fabs(e);
       }
   }
-  block_store<4>(acc, s_red, sp.partials, 0);
+  block_store<4>(acc, sm.red, sp.partials, 0);
   if (!grid_sync(sp)) return;
   double t[4];
-  grid_sum<4>(sp.partials, 0, s_res, t);
+  grid_sum<4>(sp.partials, 0, sm.res, t);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const double num = t[0] + sp.tau * t[2] - sp.tau * t[1];
     *sp.mass_defect = fabs(num) / fmax(t[3], 1e-300);
@@ -468,34 +710,58 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepParams sp) {
 }
 
 template <int L, bool C>
-void* kernel_ptr() { return (void*)step_kernel<L, C>; }
+constexpr size_t smem_bytes() {
+  constexpr int NL = C ? L : 1;
+  constexpr int NST = nstage(L, C);
+  return (size_t)(NST * 3 * NL * ABOX + NL * PN + (NT / 32) * KMAX + KMAX) * sizeof(double) +
+         NST * sizeof(uint64_t) + 128;
+}
 
-void* pick(int L, bool coupled) {
+struct KInfo {
+  void* fn;
+  size_t smem;
+};
+
+template <int L, bool C>
+KInfo info() {
+  return KInfo{(void*)step_kernel<L, C>, smem_bytes<L, C>()};
+}
+
+KInfo pick(int L, bool coupled) {
   switch (L) {
-    case 1: return coupled ? kernel_ptr<1, true>() : kernel_ptr<1, false>();
-    case 2: return coupled ? kernel_ptr<2, true>() : kernel_ptr<2, false>();
-    case 3: return coupled ? kernel_ptr<3, true>() : kernel_ptr<3, false>();
-    default: return coupled ? kernel_ptr<4, true>() : kernel_ptr<4, false>();
+    case 1: return coupled ? info<1, true>() : info<1, false>();
+    case 2: return coupled ? info<2, true>() : info<2, false>();
+    case 3: return coupled ? info<3, true>() : info<3, false>();
+    default: return coupled ? info<4, true>() : info<4, false>();
   }
+}
+
+int max_blocks_for(KInfo k, int threads, int num_sms) {
+  if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem) != cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, threads, k.smem) != cudaSuccess) return 0;
+  return per_sm * num_sms;
 }
 
 }  // namespace
 
 int mc_step_max_blocks(int L, int threads, int num_sms) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick(L, false), threads, 0) != cudaSuccess)
-    return 0;
-  int per_sm_c = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, pick(L, true), threads, 0) != cudaSuccess)
-    return 0;
-  return (per_sm < per_sm_c ? per_sm : per_sm_c) * num_sms;
+  const int a = max_blocks_for(pick(L, false), threads, num_sms);
+  const int b = max_blocks_for(pick(L, true), threads, num_sms);
+  return a < b ? a : b;
 }
+
+int mc_step_box_x() { return BX; }
+int mc_step_box_y() { return BY; }
 
 cudaError_t mc_launch_steps(mc_ctx* ctx, const StepParams& sp_in, int blocks, int threads) {
   StepParams sp = sp_in;
   sp.tiles_x = (sp.nx + TX - 1) / TX;
   sp.tiles_y = (sp.ny + TY - 1) / TY;
-  void* fn = pick(sp.L, sp.scheme == MC_SCHEME_COUPLED);
-  void* args[] = {&sp};
-  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, ctx->stream);
+  KInfo k = pick(sp.L, sp.scheme == MC_SCHEME_COUPLED);
+  cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&sp, &ctx->maps};
+  return cudaLaunchCooperativeKernel(k.fn, dim3(blocks), dim3(threads), args, k.smem, ctx->stream);
 }
