@@ -105,6 +105,8 @@ void mc_fill_params(const mc_ctx* ctx, StepParams* sp, int scheme, int nsteps);
 // Launch the persistent time-stepping kernel (mc_step.cu).
 cudaError_t mc_launch_steps(mc_ctx* ctx, const StepParams& sp, int blocks,
                             int threads);
+cudaError_t mc_launch_steps_raw(const StepParams& sp, const TmaMaps& maps, int blocks,
+                                int threads, cudaStream_t stream);
 
 // Maximum co-resident CTAs for the step kernel of this L (cooperative grid).
 int mc_step_max_blocks(int L, int threads, int num_sms);
@@ -120,6 +122,11 @@ inline int mc_pitch_for(int nx) { return (nx + 15) / 16 * 16; }
 
 // Setup kernels (mc_setup_kernels.cu).
 cudaError_t mc_launch_setup(mc_ctx* ctx, int a, const double* k_dev);
+// Context-free set-up of one continuum without exchange: TE, TN from k and
+// invd = 1 / (c h^2 / tau + sum of face T), all pitched.
+cudaError_t mc_launch_single_setup(int nx, int ny, int pitch, double h, double c, double tau,
+                                   const double* k, double* TE, double* TN, double* invd,
+                                   cudaStream_t stream);
 cudaError_t mc_launch_diag(mc_ctx* ctx, int a);
 cudaError_t mc_launch_apply(mc_ctx* ctx, int scheme, double* const* x,
                             double* const* y);

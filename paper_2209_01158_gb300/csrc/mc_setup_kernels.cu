@@ -212,3 +212,25 @@ cudaError_t mc_launch_rhs(mc_ctx* ctx, double* const* b) {
   apply_kernel<<<grid_for(ctx->Np), 256, 0, ctx->stream>>>(g);
   return cudaGetLastError();
 }
+
+cudaError_t mc_launch_single_setup(int nx, int ny, int pitch, double h, double c, double tau,
+                                   const double* k, double* TE, double* TN, double* invd,
+                                   cudaStream_t stream) {
+  const long long Np = (long long)ny * pitch;
+  faces_kernel<<<grid_for(Np), 256, 0, stream>>>(nx, ny, pitch, k, TE, TN);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  DiagArgs g{};
+  g.nx = nx;
+  g.ny = ny;
+  g.pitch = pitch;
+  g.L = 1;
+  g.a = 0;
+  g.mtau = c * h * h / tau;
+  g.TE = TE;
+  g.TN = TN;
+  g.diagc = nullptr;
+  g.invd = invd;
+  diag_kernel<<<grid_for(Np), 256, 0, stream>>>(g);
+  return cudaGetLastError();
+}

@@ -755,13 +755,19 @@ int mc_step_max_blocks(int L, int threads, int num_sms) {
 int mc_step_box_x() { return BX; }
 int mc_step_box_y() { return BY; }
 
-cudaError_t mc_launch_steps(mc_ctx* ctx, const StepParams& sp_in, int blocks, int threads) {
+cudaError_t mc_launch_steps_raw(const StepParams& sp_in, const TmaMaps& maps_in, int blocks,
+                                int threads, cudaStream_t stream) {
   StepParams sp = sp_in;
+  TmaMaps maps = maps_in;
   sp.tiles_x = (sp.nx + TX - 1) / TX;
   sp.tiles_y = (sp.ny + TY - 1) / TY;
   KInfo k = pick(sp.L, sp.scheme == MC_SCHEME_COUPLED);
   cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
   if (e != cudaSuccess) return e;
-  void* args[] = {&sp, &ctx->maps};
-  return cudaLaunchCooperativeKernel(k.fn, dim3(blocks), dim3(threads), args, k.smem, ctx->stream);
+  void* args[] = {&sp, &maps};
+  return cudaLaunchCooperativeKernel(k.fn, dim3(blocks), dim3(threads), args, k.smem, stream);
+}
+
+cudaError_t mc_launch_steps(mc_ctx* ctx, const StepParams& sp, int blocks, int threads) {
+  return mc_launch_steps_raw(sp, ctx->maps, blocks, threads, ctx->stream);
 }
