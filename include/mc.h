@@ -180,6 +180,50 @@ mc_status mc_rhs_decoupled(mc_ctx* ctx, double* const* b);
 /* Bytes of device memory the context holds. */
 mc_status mc_device_bytes(const mc_ctx* ctx, int64_t* bytes);
 
+/*
+ * mc_step_single_noalloc -- nsteps backward-Euler steps of ONE continuum,
+ *   (M/tau + D) p^n = M/tau p^{n-1} + F   (no exchange; h = 1/nx),
+ * for callers that cannot allocate device memory. The paper has no
+ * counterpart: this is a deployment variant of mc_step_decoupled with L = 1.
+ *
+ * Who needs it: code that runs where a cudaMalloc is not allowed or not
+ * affordable -- inside a framework whose caching allocator owns the device
+ * memory, in a long-running service whose memory budget is fixed at start-up,
+ * or in a latency-bound loop where cudaMalloc/cudaFree (which can synchronise
+ * the device) must not appear. Such a caller owns its input and output
+ * buffers and only wants the solver's own scratch to come from somewhere.
+ *
+ * This entry point creates no context and calls no cudaMalloc, cudaFree or
+ * other allocating routine. All of its scratch (pitched copies of the fields,
+ * transmissibilities, PCG vectors, partial sums, barrier words, statistics)
+ * lives in one fixed device array of the library, about 5.5 MB, which every
+ * GPU that loads the library holds until the process exits.
+ *
+ *   nx, ny    grid; ny * (nx rounded up to 16) must be <= 65536 cells
+ *             (e.g. 256 x 256), else MC_E_ARG.
+ *   k         DEVICE pointer, nx*ny permeabilities (row-major, x fastest),
+ *             finite and >= 0; read only.
+ *   c, tau    c > 0 (M = c h^2), time step tau > 0.
+ *   F         DEVICE pointer, nx*ny cell-integrated sources; read only.
+ *   p         DEVICE pointer, nx*ny state: read as p^0, overwritten with the
+ *             state after the last completed step (on MC_E_NOCONV,
+ *             MC_E_BREAKDOWN or MC_E_TIMEOUT: the start of the failed step).
+ *   rtol, max_iter  PCG stop ||r|| <= rtol ||b|| per step, iteration cap.
+ *   stream    cudaStream_t (NULL: legacy default); the call synchronises it.
+ *   stats     host, may be NULL: iters[0], max_iters[0], rel_residual[0],
+ *             steps_done, status, mass_defect.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Every call shares the one array and starts by zeroing it, so two
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and corrupt each other: serialise them.
+ */
+mc_status mc_step_single_noalloc(int32_t nx, int32_t ny, const double* k, double c,
+                                 double tau, const double* F, double* p, int32_t nsteps,
+                                 double rtol, int32_t max_iter, void* stream,
+                                 mc_stats* stats);
+
 void mc_destroy(mc_ctx* ctx);
 
 /* Last error text of ctx (or of the last failed mc_setup when ctx is NULL). */

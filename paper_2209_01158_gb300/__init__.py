@@ -205,6 +205,30 @@ def mc_device_bytes(ctx):
     return v.value
 
 
+def _dev_ptr(x):
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda or str(x.dtype) != "torch.float64" or not x.is_contiguous():
+            raise ValueError("device buffers must be contiguous CUDA float64 tensors")
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(int(x))
+
+
+def mc_step_single_noalloc(nx, ny, k, c, tau, F, p, nsteps, rtol=1e-12, max_iter=100000,
+                           stream=None, check=True):
+    """Single-continuum steps with no device allocation (see include/mc.h).
+    k, F, p: CUDA float64 tensors (or raw device pointers) of nx*ny values;
+    p is updated in place."""
+    s = N.mc_stats()
+    st = _lib().mc_step_single_noalloc(int(nx), int(ny), _dev_ptr(k), float(c), float(tau),
+                                       _dev_ptr(F), _dev_ptr(p), int(nsteps), float(rtol),
+                                       int(max_iter), _stream_handle(stream), C.byref(s))
+    d = _stats_dict(s, 1)
+    d["return"] = st
+    if check and st != N.MC_OK:
+        raise MCError(st, _lib().mc_status_string(st).decode())
+    return d
+
+
 def mc_destroy(ctx):
     if ctx:
         _lib().mc_destroy(ctx)

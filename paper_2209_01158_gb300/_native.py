@@ -57,6 +57,10 @@ SIGNATURES = {
     "mc_apply": (C.c_int, [C.c_void_p, C.c_int32, dpp, dpp]),
     "mc_rhs_decoupled": (C.c_int, [C.c_void_p, dpp]),
     "mc_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "mc_step_single_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_double,
+                                         C.c_double, C.c_void_p, C.c_void_p, C.c_int32,
+                                         C.c_double, C.c_int32, C.c_void_p,
+                                         C.POINTER(mc_stats)]),
     "mc_destroy": (None, [C.c_void_p]),
     "mc_last_error": (C.c_char_p, [C.c_void_p]),
     "mc_status_string": (C.c_char_p, [C.c_int]),
