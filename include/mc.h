@@ -180,6 +180,51 @@ mc_status mc_rhs_decoupled(mc_ctx* ctx, double* const* b);
 /* Bytes of device memory the context holds. */
 mc_status mc_device_bytes(const mc_ctx* ctx, int64_t* bytes);
 
+/* ---------------- NLMC coarse model (Section 4) ---------------------------
+ *
+ * mc_nlmc_build -- multiscale basis and coarse operator for a context whose
+ * grid divides into ncx x ncy coarse blocks (nx % ncx == ny % ncy == 0).
+ *   Basis (Section 4.1, Eq. eq:basis): for every coarse block K_i and
+ *   continuum beta, psi^{i,beta} on K_i^+ = K_i grown by `layers` coarse
+ *   layers (clipped to the domain) minimises the energy of the coupled fine
+ *   operator D + Q on K_i^+ with zero Dirichlet data on the part of its
+ *   boundary inside the domain (ghost at h/2, T = 2k) subject to
+ *   mean_{K_j}(psi_alpha) = delta_ij delta_alpha,beta for every K_j in K_i^+.
+ *   Solved by projected Jacobi-PCG in the constraint null space to a
+ *   preconditioned-residual reduction basis_rtol (at most basis_max_iter
+ *   iterations; MC_E_NOCONV otherwise).
+ *   Coarse operator: A_bar = R (D + Q) R^T; M_bar = diag(c_a |K_i|);
+ *   F_bar = block sums of the context's current sources; the coarse state
+ *   starts as the block means of the context's current state.
+ * Coarse index (alpha, i) -> alpha * ncx*ncy + i, i = J*ncx + I.
+ * The context must outlive the returned object.
+ */
+mc_status mc_nlmc_build(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
+                        double basis_rtol, int32_t basis_max_iter, mc_nlmc** out);
+
+/* nsteps coarse steps: MC_SCHEME_COUPLED (Eq. is-nlmc) or the D-, L-,
+ * U-schemes of Section 4.3 (A0_bar = diagonal / lower / upper blocks of
+ * A_bar). Each coarse solve: explicit inverse (formed once) + one residual
+ * correction. stats: steps_done, status. */
+mc_status mc_nlmc_step(mc_nlmc* m, int32_t scheme, int32_t nsteps, mc_stats* stats);
+
+/* Coarse state, L * ncx * ncy doubles (host). */
+mc_status mc_nlmc_set_state(mc_nlmc* m, const double* pbar);
+mc_status mc_nlmc_get_state(mc_nlmc* m, double* pbar);
+
+/* A_bar ((L Nc)^2 row-major), M_bar and F_bar (L Nc each); any may be NULL. */
+mc_status mc_nlmc_get_operator(mc_nlmc* m, double* Abar, double* mbar, double* fbar);
+
+/* psi^{block,beta} as L fine fields (L * nx * ny host doubles, zero outside
+ * the oversampled region). */
+mc_status mc_nlmc_get_basis(mc_nlmc* m, int32_t block, int32_t beta, double* psi);
+
+/* info[0..4] = Nc, L, total basis PCG iterations, largest basis iteration
+ * count, device bytes held. */
+mc_status mc_nlmc_info(const mc_nlmc* m, int64_t* info);
+
+void mc_nlmc_destroy(mc_nlmc* m);
+
 /*
  * mc_step_single_noalloc -- nsteps backward-Euler steps of ONE continuum,
  *   (M/tau + D) p^n = M/tau p^{n-1} + F   (no exchange; h = 1/nx),

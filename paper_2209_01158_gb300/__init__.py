@@ -234,6 +234,66 @@ def mc_destroy(ctx):
         _lib().mc_destroy(ctx)
 
 
+class NLMC:
+    """Owning wrapper of an mc_nlmc built on a Context (which must stay open)."""
+
+    def __init__(self, ctx, ncx, ncy, layers, basis_rtol=1e-12, basis_max_iter=50000):
+        self.ctx = ctx
+        self.ncx, self.ncy, self.L = int(ncx), int(ncy), ctx.L
+        self.n = self.L * self.ncx * self.ncy
+        h = C.c_void_p()
+        st = _lib().mc_nlmc_build(ctx.handle, int(ncx), int(ncy), int(layers), float(basis_rtol),
+                                  int(basis_max_iter), C.byref(h))
+        _check(st, ctx.handle)
+        self._h = h
+
+    def step(self, scheme="D", nsteps=1):
+        sc = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+        s = N.mc_stats()
+        st = _lib().mc_nlmc_step(self._h, int(sc), int(nsteps), C.byref(s))
+        _check(st, self.ctx.handle)
+        return {"steps_done": s.steps_done}
+
+    def get_state(self):
+        out = np.empty(self.n)
+        _check(_lib().mc_nlmc_get_state(self._h, out.ctypes.data_as(N.dp)))
+        return out
+
+    def set_state(self, pbar):
+        a = np.ascontiguousarray(pbar, dtype=np.float64)
+        _check(_lib().mc_nlmc_set_state(self._h, a.ctypes.data_as(N.dp)))
+
+    def operator(self):
+        A = np.empty((self.n, self.n))
+        m = np.empty(self.n)
+        f = np.empty(self.n)
+        _check(_lib().mc_nlmc_get_operator(self._h, A.ctypes.data_as(N.dp), m.ctypes.data_as(N.dp),
+                                           f.ctypes.data_as(N.dp)))
+        return A, m, f
+
+    def basis(self, block, beta):
+        out = np.empty(self.L * self.ctx.n)
+        _check(_lib().mc_nlmc_get_basis(self._h, int(block), int(beta), out.ctypes.data_as(N.dp)))
+        return out
+
+    def info(self):
+        v = (C.c_int64 * 5)()
+        _check(_lib().mc_nlmc_info(self._h, v))
+        return {"Nc": v[0], "L": v[1], "basis_iters": v[2], "basis_iters_max": v[3],
+                "device_bytes": v[4]}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().mc_nlmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """Owning wrapper around an mc_ctx for one workload on one stream."""
 

@@ -61,6 +61,15 @@ SIGNATURES = {
                                          C.c_double, C.c_void_p, C.c_void_p, C.c_int32,
                                          C.c_double, C.c_int32, C.c_void_p,
                                          C.POINTER(mc_stats)]),
+    "mc_nlmc_build": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                C.c_int32, C.POINTER(C.c_void_p)]),
+    "mc_nlmc_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(mc_stats)]),
+    "mc_nlmc_set_state": (C.c_int, [C.c_void_p, dp]),
+    "mc_nlmc_get_state": (C.c_int, [C.c_void_p, dp]),
+    "mc_nlmc_get_operator": (C.c_int, [C.c_void_p, dp, dp, dp]),
+    "mc_nlmc_get_basis": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, dp]),
+    "mc_nlmc_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "mc_nlmc_destroy": (None, [C.c_void_p]),
     "mc_destroy": (None, [C.c_void_p]),
     "mc_last_error": (C.c_char_p, [C.c_void_p]),
     "mc_status_string": (C.c_char_p, [C.c_int]),

@@ -281,6 +281,7 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
   for (int a = 0; a < L; ++a) {
     bool percell = false;
     for (int b = 0; b < L; ++b) percell |= (ctx->qcell[a][b] != nullptr);
+    CKS(mc_alloc(ctx, (void**)&ctx->k[a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->TE[a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->TN[a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->invd[a], fb));
@@ -307,11 +308,10 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
   CKS(mc_alloc(ctx, (void**)&ctx->dmaxit, MCL * sizeof(int)));
   CKS(mc_alloc(ctx, (void**)&ctx->drelres, MCL * sizeof(double)));
   CKS(mc_alloc(ctx, (void**)&ctx->dmass, sizeof(double)));
-  // Coefficients: k goes through the r buffer (work space, free until the
-  // first step) into TE / TN.
+  // Coefficients: k (kept on the device for the NLMC build) into TE / TN.
   for (int a = 0; a < L; ++a) {
-    CKS(h2d(ctx, ctx->r[a], k[a]));
-    CKS(mc_launch_setup(ctx, a, ctx->r[a]));
+    CKS(h2d(ctx, ctx->k[a], k[a]));
+    CKS(mc_launch_setup(ctx, a, ctx->k[a]));
   }
   for (int a = 0; a < L; ++a) CKS(mc_launch_diag(ctx, a));
   // TMA descriptors of the tiles the stencil phase stages in shared memory.

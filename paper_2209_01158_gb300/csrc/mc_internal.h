@@ -71,6 +71,7 @@ struct mc_ctx {
   mc_opts opts{};
   int num_sms = 0;
   // device buffers
+  double* k[MCL] = {};      // permeability (pitched), kept for the NLMC build
   double* TE[MCL] = {};
   double* TN[MCL] = {};
   double* invd[MCL] = {};

@@ -28,6 +28,7 @@
 #include <math.h>
 
 #include "mc_internal.h"
+#include "mc_sync.cuh"
 #include "mc_tma.h"
 
 namespace {
@@ -53,62 +54,27 @@ __host__ __device__ constexpr int nstage(int L, bool coupled) {
 __device__ __forceinline__ double ldc(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ double ldr(const double* p) { return __ldg(p); }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
+__device__ __forceinline__ double warp_sum(double v) { return warp_sum_d(v); }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+__device__ __forceinline__ GridBar bar_of(const StepParams& sp) {
+  GridBar g;
+  g.count = reinterpret_cast<unsigned long long*>(sp.bar_count);
+  g.abort_word = sp.bar_gen + 32;
+  g.status = sp.status;
+  g.spin_limit = sp.spin_limit;
+  return g;
 }
 
 __device__ __forceinline__ void raise_abort(const StepParams& sp, int code) {
-  atomicExch(sp.bar_gen + 32, 1u);
-  atomicCAS(sp.status, 0, code);
+  grid_raise_abort(bar_of(sp), code);
 }
 
-// Grid-wide barrier for a cooperative launch. Every wait is bounded by
-// spin_limit polls; a CTA that gives up raises the abort word and the status
-// MC_E_TIMEOUT, and every CTA that sees the abort word leaves the kernel.
+// Grid-wide barrier (mc_sync.cuh); afterwards thread 0, which issues the TMA
+// loads, orders the other CTAs' generic stores before its async-proxy reads.
 __device__ bool grid_sync(const StepParams& sp) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    unsigned* count = sp.bar_count;
-    unsigned* gen = sp.bar_gen;
-    unsigned* abort_word = sp.bar_gen + 32;
-    unsigned g = ld_acquire(gen);
-    __threadfence();
-    unsigned arrived = atomicAdd(count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      long long n = 0;
-      while (ld_acquire(gen) == g) {
-        if (ld_acquire(abort_word) != 0u) { ok = 0; break; }
-        if (++n > sp.spin_limit) {
-          raise_abort(sp, (int)MC_E_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-    if (ok && ld_acquire(abort_word) != 0u) ok = 0;
-    // Other CTAs' generic stores are now visible; order them before this
-    // thread's later TMA reads.
-    fence_proxy_async();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
+  const bool ok = grid_barrier(bar_of(sp));
+  if (threadIdx.x == 0) fence_proxy_async();
+  return ok;
 }
 
 template <int NQ>

@@ -1,0 +1,103 @@
+// Grid-wide synchronisation and deterministic reductions for the persistent
+// (cooperative) kernels of libmc.so.
+//
+// The barrier is a monotonic 64-bit arrival counter: barrier number b is
+// passed when the counter reaches (b + 1) * gridDim.x, so one release atomic
+// per CTA and acquire polls suffice (no reset, no generation word). Every
+// wait is bounded by `spin_limit` polls; a CTA that gives up raises the abort
+// word and the status MC_E_TIMEOUT, and CTAs that see the abort word while
+// waiting leave too, so no launch can hang.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mc.h"
+
+struct GridBar {
+  unsigned long long* count;  // zeroed before the launch
+  unsigned* abort_word;       // zeroed before the launch
+  int* status;
+  long long spin_limit;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long long* p,
+                                                                   unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void grid_raise_abort(const GridBar& g, int code) {
+  atomicExch(g.abort_word, 1u);
+  atomicCAS(g.status, 0, code);
+}
+
+// Returns false when the launch must stop (timeout here or abort elsewhere).
+// Thread 0 of each CTA does the arrival; the rest wait at the CTA barrier.
+__device__ __forceinline__ bool grid_barrier(const GridBar& g) {
+  __shared__ int s_grid_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    const unsigned long long G = gridDim.x;
+    const unsigned long long old = atom_add_release_u64(g.count, 1ull);
+    const unsigned long long target = (old / G + 1ull) * G;
+    long long n = 0;
+    while (ld_acquire_u64(g.count) < target) {
+      ++n;
+      if ((n & 63) == 0 && ld_acquire_u32(g.abort_word) != 0u) { ok = 0; break; }
+      if (n > g.spin_limit) {
+        grid_raise_abort(g, (int)MC_E_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    s_grid_ok = ok;
+  }
+  __syncthreads();
+  return s_grid_ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic CTA sum of NQ values; every thread receives the totals.
+// s_red needs (blockDim.x / 32) * NQ doubles, s_res NQ doubles.
+template <int NQ>
+__device__ __forceinline__ void cta_sum(double (&v)[NQ], double* s_red, double* s_res) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const double s = warp_sum_d(v[k]);
+    if (lane == 0) s_red[warp * NQ + k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += s_red[w * NQ + threadIdx.x];
+    s_res[threadIdx.x] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) v[k] = s_res[k];
+  __syncthreads();
+}
