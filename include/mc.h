@@ -72,10 +72,13 @@ typedef struct {
   int32_t precision;   /* MC_PREC_*: FP64 PCG, or FP32 / BF16-transmissibility
                           inner PCG inside FP64 iterative refinement */
   int32_t precond;     /* MC_PRECOND_JACOBI */
-  int32_t max_iter;    /* PCG iterations per solve (inner iterations for IR) */
+  int32_t max_iter;    /* PCG iterations per solve (IR forms: cap of each inner
+                          solve, further limited to 4 max(nx, ny) (>= 512);
+                          an inner solve also stops when FP32 stagnates) */
   int32_t ir_max;      /* maximum refinement sweeps per solve (IR forms) */
   double rtol;         /* stop when ||b - A x||_2 <= rtol ||b||_2 (FP64) */
-  double inner_rtol;   /* inner PCG relative target of each IR sweep */
+  double inner_rtol;   /* inner PCG relative residual target of each IR sweep
+                          (default 1e-3) */
   int64_t spin_limit;  /* polls of a grid barrier before MC_E_TIMEOUT */
   int32_t blocks;      /* persistent CTAs (0: one per SM x occupancy) */
   int32_t threads;     /* threads per CTA (0: default 512) */

@@ -169,7 +169,7 @@ mc_status mc_default_opts(mc_opts* o) {
   o->max_iter = 100000;
   o->ir_max = 50;
   o->rtol = 1e-12;
-  o->inner_rtol = 1e-4;
+  o->inner_rtol = 1e-3;
   o->spin_limit = 2000000;
   o->blocks = 0;
   o->threads = 0;
@@ -299,7 +299,8 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
     cuda_err(ctx, "occupancy query", cudaGetLastError());
     return bail(MC_E_CUDA);
   }
-  ctx->partials_len = (size_t)2 * 4 * MCL * maxb;
+  ctx->maxb = maxb;
+  ctx->partials_len = (size_t)2 * MC_KMAX_ALLOC * maxb;
   CKS(mc_alloc(ctx, (void**)&ctx->partials, ctx->partials_len * sizeof(double)));
   CKS(mc_alloc(ctx, (void**)&ctx->bar, 96 * sizeof(unsigned)));
   CKS(mc_alloc(ctx, (void**)&ctx->dstatus, sizeof(int)));
@@ -308,6 +309,7 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
   CKS(mc_alloc(ctx, (void**)&ctx->dmaxit, MCL * sizeof(int)));
   CKS(mc_alloc(ctx, (void**)&ctx->drelres, MCL * sizeof(double)));
   CKS(mc_alloc(ctx, (void**)&ctx->dmass, sizeof(double)));
+  CKS(mc_alloc(ctx, (void**)&ctx->dsweeps, sizeof(int)));
   // Coefficients: k (kept on the device for the NLMC build) into TE / TN.
   for (int a = 0; a < L; ++a) {
     CKS(h2d(ctx, ctx->k[a], k[a]));
@@ -390,8 +392,9 @@ mc_status mc_state_device(mc_ctx* ctx, int32_t alpha, double** dev) {
 static mc_status run_steps(mc_ctx* ctx, int scheme, int nsteps, mc_stats* stats) {
   if (stats) memset(stats, 0, sizeof(*stats));
   if (nsteps < 0) return set_err(ctx, MC_E_ARG, "nsteps < 0");
-  if (ctx->opts.precision != MC_PREC_FP64)
-    return set_err(ctx, MC_E_ARG, "this precision form is not available for this entry point");
+  const bool ir = ctx->opts.precision != MC_PREC_FP64;
+  if (ir && scheme == MC_SCHEME_COUPLED)
+    return set_err(ctx, MC_E_ARG, "the precision form applies to the decoupled schemes");
   if (nsteps == 0) return MC_OK;
   CK(cudaSetDevice(ctx->device));
   StepParams sp;
@@ -403,8 +406,19 @@ static mc_status run_steps(mc_ctx* ctx, int scheme, int nsteps, mc_stats* stats)
   CK(cudaMemsetAsync(ctx->dmaxit, 0, MCL * sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(ctx->drelres, 0, MCL * sizeof(double), ctx->stream));
   CK(cudaMemsetAsync(ctx->dmass, 0, sizeof(double), ctx->stream));
-  const int blocks = launch_blocks(ctx);
-  CK(mc_launch_steps(ctx, sp, blocks, launch_threads(ctx)));
+  CK(cudaMemsetAsync(ctx->dsweeps, 0, sizeof(int), ctx->stream));
+  if (ir) {
+    const int bf16 = ctx->opts.precision == MC_PREC_BF16T_IR ? 1 : 0;
+    CK(mc_ir_prepare(ctx, bf16));
+    int blocks = mc_ir_max_blocks(ctx->L, bf16 != 0, ctx->num_sms);
+    if (blocks > ctx->maxb) blocks = ctx->maxb;
+    if (ctx->opts.blocks > 0 && ctx->opts.blocks < blocks) blocks = ctx->opts.blocks;
+    if (blocks < 1) return set_err(ctx, MC_E_CUDA, "no co-resident CTAs for the precision form");
+    CK(mc_launch_ir(ctx, sp, bf16, blocks));
+  } else {
+    const int blocks = launch_blocks(ctx);
+    CK(mc_launch_steps(ctx, sp, blocks, launch_threads(ctx)));
+  }
   int st = 0, done = 0;
   mc_stats s;
   memset(&s, 0, sizeof(s));
@@ -414,6 +428,7 @@ static mc_status run_steps(mc_ctx* ctx, int scheme, int nsteps, mc_stats* stats)
   CK(cudaMemcpyAsync(s.max_iters, ctx->dmaxit, MCL * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(s.rel_residual, ctx->drelres, MCL * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&s.mass_defect, ctx->dmass, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&s.ir_sweeps, ctx->dsweeps, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   s.steps_done = done;
   s.status = st;

@@ -11,6 +11,8 @@
 #include "../../include/mc.h"
 
 #define MCL MC_MAX_CONTINUA
+// partial-sum quantities reserved per reduction slot (all persistent kernels)
+#define MC_KMAX_ALLOC (8 * MCL)
 
 // Everything the persistent time-stepping kernel needs, passed by value.
 // Field pointers address ny rows of `pitch` doubles, cell (i, j) at
@@ -59,6 +61,21 @@ struct TmaMaps {
   CUtensorMap invd[MCL];
 };
 
+// Extra state of the precision form (FP32 inner PCG in FP64 refinement).
+struct IrParams {
+  StepParams sp;                 // FP64 state, coefficients, outer residual in sp.r
+  float* r32[MCL];
+  float* P32[2][MCL];
+  float* q32[MCL];
+  float* d32[MCL];
+  const float* invd32[MCL];
+  const void* TElo[MCL];         // float or bf16 transmissibilities
+  const void* TNlo[MCL];
+  double inner_rtol;
+  int ir_max;
+  int* ir_sweeps;
+};
+
 struct mc_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -85,6 +102,18 @@ struct mc_ctx {
   double* q[MCL] = {};
   double* partials = nullptr;
   size_t partials_len = 0;
+  int maxb = 0;                    // CTAs the partials buffer is sized for
+  // precision form (allocated on first use)
+  float* r32[MCL] = {};
+  float* P32[2][MCL] = {};
+  float* q32[MCL] = {};
+  float* d32[MCL] = {};
+  float* invd32[MCL] = {};
+  float* TElo32[MCL] = {};         // FP32 copies, or BF16 in their first half
+  float* TNlo32[MCL] = {};
+  int lo_kind = 0;                 // 0 none, 1 FP32, 2 BF16
+  TmaMaps maps32;
+  int* dsweeps = nullptr;
   unsigned* bar = nullptr;         // [0] count, [32] generation (own sector)
   int* dstatus = nullptr;
   int* dsteps = nullptr;
@@ -113,6 +142,11 @@ cudaError_t mc_launch_steps_raw(const StepParams& sp, const TmaMaps& maps, int b
 int mc_step_max_blocks(int L, int threads, int num_sms);
 int mc_step_box_x();
 int mc_step_box_y();
+
+// Precision form (mc_ir.cu).
+int mc_ir_max_blocks(int L, bool bf16, int num_sms);
+cudaError_t mc_ir_prepare(mc_ctx* ctx, int bf16);
+cudaError_t mc_launch_ir(mc_ctx* ctx, const StepParams& sp, int bf16, int blocks);
 
 // Encode a 2-D tiled tensor map (x innermost) over a pitched array.
 cudaError_t mc_encode_map(CUtensorMap* map, CUtensorMapDataType dtype, int esize, void* base,

@@ -1,0 +1,617 @@
+// Precision form of the decoupled step: FP32 inner PCG inside FP64 iterative
+// refinement, one persistent cooperative launch per call.
+//
+// Each continuum's system of the D-, L- or U-scheme (Section 3.3)
+//   (M_a/tau + D_a + sum_b Q_ab) x = b
+// is solved by refinement sweeps:
+//   1. FP64 residual, flux form, every term a difference of nearby values:
+//        r = F + m/tau (p^{n-1} - x) + sum_b q_ab (p_b - x) - D x
+//   2. constant-mode deflation: the exact solution satisfies 1^T r = 0
+//      (1^T D = 0), so x += c, r -= c diag(A0 - D) with
+//      c = 1^T r / 1^T diag(A0 - D); the FP32 solve cannot resolve this
+//      near-null mode, the FP64 shift does;
+//   3. stop when ||r|| <= rtol ||b|| (FP64);
+//   4. FP32 PCG on A d = r (transmissibilities stored FP32 or BF16, FP32
+//      vectors, Jacobi), to a relative residual inner_rtol; the dot products
+//      are summed per thread in FP32 and then across the grid in FP64;
+//   5. x += d in FP64.
+// The inner iteration has the structure of the FP64 kernel (TMA halo tiles of
+// r, P_old and invd in a shared-memory ring, then a pointwise vector phase),
+// with 4-byte data.
+
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "mc_internal.h"
+#include "mc_sync.cuh"
+#include "mc_tma.h"
+
+namespace {
+
+constexpr int TX = 64, TY = 16;
+constexpr int HOFF = 4;                 // 16 B of floats left of the tile
+constexpr int BX = TX + 2 * HOFF;       // 72 floats, 288 B rows
+constexpr int BY = TY + 2;
+constexpr int ABOX = 1312;              // floats per box slot (5248 B, 128-B multiple)
+constexpr uint32_t BOX_BYTES = BX * BY * 4;
+constexpr int PX = TX + 2, PN = PX * BY;
+constexpr int NT = 512;
+constexpr int RPT = NT / TX;            // 8 tile rows per pass of the CTA
+constexpr int CPT = TY / RPT;           // 2 own cells per thread
+constexpr int NST = 6;
+constexpr int KM = MC_KMAX_ALLOC;
+
+__device__ __forceinline__ float tload(const float* p, long long i) { return __ldg(p + i); }
+__device__ __forceinline__ float tload(const __nv_bfloat16* p, long long i) {
+  return __bfloat162float(p[i]);
+}
+
+__device__ __forceinline__ GridBar irbar(const StepParams& sp) {
+  GridBar g;
+  g.count = reinterpret_cast<unsigned long long*>(sp.bar_count);
+  g.abort_word = sp.bar_gen + 32;
+  g.status = sp.status;
+  g.spin_limit = sp.spin_limit;
+  return g;
+}
+
+__device__ __forceinline__ bool gsync(const StepParams& sp) {
+  const bool ok = grid_barrier(irbar(sp));
+  if (threadIdx.x == 0) fence_proxy_async();
+  return ok;
+}
+
+template <int NQ>
+__device__ void store_part(double (&v)[NQ], double* s_red, double* partials, int slot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const double s = warp_sum_d(v[k]);
+    if (lane == 0) s_red[warp * NQ + k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += s_red[w * NQ + threadIdx.x];
+    partials[((size_t)slot * KM + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+template <int NQ>
+__device__ void sum_part(const double* partials, int slot, double* s_res, double (&out)[NQ]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nb = gridDim.x;
+  for (int k = warp; k < NQ; k += NT / 32) {
+    const double* src = partials + ((size_t)slot * KM + k) * nb;
+    double s = 0.0;
+#pragma unroll 4
+    for (int b = lane; b < nb; b += 32) s += __ldcg(src + b);
+    s = warp_sum_d(s);
+    if (lane == 0) s_res[k] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) out[k] = s_res[k];
+  __syncthreads();
+}
+
+__device__ __forceinline__ double qab(const StepParams& sp, int a, int b, long long i) {
+  const double* c = sp.qcell[a][b];
+  return c ? __ldg(c + i) : sp.qconst[a][b];
+}
+
+__device__ __forceinline__ double dcell(const StepParams& sp, int a, long long i) {
+  const double* d = sp.diagc[a];
+  return d ? __ldg(d + i) : sp.diagc_const[a];
+}
+
+struct Sm {
+  float* box;      // [NST][3][ABOX]
+  float* pn;       // [PN]
+  double* red;     // [NT/32][KM]
+  double* res;     // [KM]
+  uint64_t* bar;   // [NST]
+};
+
+// One solve of the continua in `mask` (all at once for D; one for L/U).
+template <int L, typename TT>
+__device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask, Sm& sm,
+                         uint32_t& phb, int& slot) {
+  const StepParams& sp = ip.sp;
+  const int nx = sp.nx, ny = sp.ny, pitch = sp.pitch;
+  const long long Np = sp.Np;
+  const int tid = threadIdx.x;
+  const long long gtid = (long long)blockIdx.x * NT + tid;
+  const long long gs = (long long)gridDim.x * NT;
+  const bool lag_prev = sp.scheme == MC_SCHEME_D;
+  const double rtol2 = sp.rtol * sp.rtol;
+  const double in2 = ip.inner_rtol * ip.inner_rtol;
+  double bb[L];
+#pragma unroll
+  for (int a = 0; a < L; ++a) bb[a] = 0.0;
+  unsigned active = mask;
+  int its[L];
+#pragma unroll
+  for (int a = 0; a < L; ++a) its[a] = 0;
+  int sweeps = 0;
+  bool ok = true;
+  for (int sweep = 0; ok; ++sweep) {
+    // ---- 1. FP64 residual and the sums of the constant-mode correction -----
+    // q: [rr, sum r, sum dc, sum r dc, sum dc^2, bb] per continuum
+    double acc[6 * L];
+#pragma unroll
+    for (int k = 0; k < 6 * L; ++k) acc[k] = 0.0;
+#pragma unroll
+    for (int a = 0; a < L; ++a) {
+      if (!(active & (1u << a))) continue;
+      const double* x = sp.p[a];
+      for (long long i = gtid; i < Np; i += gs) {
+        const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+        if (gx >= nx) continue;
+        const double xc = __ldcg(x + i);
+        const double xp = __ldcg(sp.pprev[a] + i);
+        const double f = __ldg(sp.F[a] + i);
+        double rv = f + sp.mtau[a] * (xp - xc);
+        double bv = sp.mtau[a] * xp + f;
+#pragma unroll
+        for (int b = 0; b < L; ++b) {
+          if (b == a) continue;
+          const double pb = lag_prev ? __ldcg(sp.pprev[b] + i) : __ldcg(sp.p[b] + i);
+          const double qv = qab(sp, a, b, i);
+          rv += qv * (pb - xc);
+          bv += qv * pb;
+        }
+        if (gx + 1 < nx) rv -= __ldg(sp.TE[a] + i) * (xc - __ldcg(x + i + 1));
+        if (gx > 0) rv -= __ldg(sp.TE[a] + i - 1) * (xc - __ldcg(x + i - 1));
+        if (gy + 1 < ny) rv -= __ldg(sp.TN[a] + i) * (xc - __ldcg(x + i + pitch));
+        if (gy > 0) rv -= __ldg(sp.TN[a] + i - pitch) * (xc - __ldcg(x + i - pitch));
+        const double dc = dcell(sp, a, i);
+        sp.r[a][i] = rv;
+        acc[a] += rv * rv;
+        acc[L + a] += rv;
+        acc[2 * L + a] += dc;
+        acc[3 * L + a] += rv * dc;
+        acc[4 * L + a] += dc * dc;
+        acc[5 * L + a] += bv * bv;
+      }
+    }
+    store_part<6 * L>(acc, sm.red, sp.partials, slot);
+    if (!gsync(sp)) return false;
+    double t[6 * L];
+    sum_part<6 * L>(sp.partials, slot, sm.res, t);
+    slot ^= 1;
+    double shift[L];
+    unsigned inner = 0;
+#pragma unroll
+    for (int a = 0; a < L; ++a) {
+      shift[a] = 0.0;
+      if (!(active & (1u << a))) continue;
+      if (sweep == 0) bb[a] = t[5 * L + a];
+      const double c = t[2 * L + a] > 0.0 ? t[L + a] / t[2 * L + a] : 0.0;
+      shift[a] = c;
+      const double rr = t[a] - 2.0 * c * t[3 * L + a] + c * c * t[4 * L + a];
+      if (rr > rtol2 * bb[a]) inner |= 1u << a;
+    }
+    if (inner && sweep >= ip.ir_max) {
+      if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_NOCONV);
+      return false;
+    }
+    // ---- 2. apply the shift; start the inner solve on the corrected residual
+    double acc2[2 * L];
+#pragma unroll
+    for (int k = 0; k < 2 * L; ++k) acc2[k] = 0.0;
+#pragma unroll
+    for (int a = 0; a < L; ++a) {
+      if (!(active & (1u << a))) continue;
+      const double c = shift[a];
+      const bool go = inner & (1u << a);
+      for (long long i = gtid; i < Np; i += gs) {
+        const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+        if (gx >= nx) continue;
+        sp.p[a][i] = __ldcg(sp.p[a] + i) + c;
+        if (go) {
+          const double rv = __ldcg(sp.r[a] + i) - c * dcell(sp, a, i);
+          const float r32 = (float)rv;
+          const float z = __ldg(ip.invd32[a] + i) * r32;
+          ip.r32[a][i] = r32;
+          ip.d32[a][i] = 0.0f;
+          ip.P32[0][a][i] = z;
+          acc2[a] += (double)r32 * (double)r32;
+          acc2[L + a] += (double)r32 * (double)z;
+        }
+      }
+    }
+    active = inner;
+    if (!active) break;
+    ++sweeps;
+    store_part<2 * L>(acc2, sm.red, sp.partials, slot);
+    if (!gsync(sp)) return false;
+    double t2[2 * L];
+    sum_part<2 * L>(sp.partials, slot, sm.res, t2);
+    slot ^= 1;
+    double rr0[L], rz[L], beta[L], rr[L], rck[L];
+#pragma unroll
+    for (int a = 0; a < L; ++a) {
+      rr0[a] = t2[a];
+      rr[a] = t2[a];
+      rck[a] = t2[a];
+      rz[a] = t2[L + a];
+      beta[a] = 0.0;
+    }
+    // ---- 3. FP32 inner PCG ----------------------------------------------------
+    unsigned act = 0;
+#pragma unroll
+    for (int a = 0; a < L; ++a)
+      if ((active & (1u << a)) && rr0[a] > 0.0) act |= 1u << a;
+    int cur = 0;
+    int it = 0;
+    const int tiles = sp.tiles_x * sp.tiles_y;
+    const int lx = tid % TX, ly = tid / TX;
+    // inner iterations per sweep: restarting the FP32 CG from the refined
+    // FP64 residual beats a long stalled FP32 run
+    int inner_cap = 4 * (nx > ny ? nx : ny);
+    if (inner_cap < 512) inner_cap = 512;
+    if (inner_cap > sp.max_iter) inner_cap = sp.max_iter;
+    while (act) {
+      if (it >= inner_cap) break;  // the outer loop measures what was reached
+      int alist[L];
+      int nact = 0;
+#pragma unroll
+      for (int a = 0; a < L; ++a) if (act & (1u << a)) alist[nact++] = a;
+      double pq[L];
+#pragma unroll
+      for (int a = 0; a < L; ++a) pq[a] = 0.0;
+      const int ntask = nact * tiles;
+      auto issue = [&](int task, int s) {
+        const int w = task / tiles, tt = task - w * tiles;
+        int a0 = 0;
+#pragma unroll
+        for (int k = 0; k < L; ++k) if (k == w) a0 = alist[k];
+        const int bx0 = (tt % sp.tiles_x) * TX - HOFF;
+        const int by0 = (tt / sp.tiles_x) * TY - 1;
+        uint64_t* bar = sm.bar + s;
+        fence_proxy_async();
+        mbar_expect_tx(bar, 3 * BOX_BYTES);
+        float* base = sm.box + (size_t)s * 3 * ABOX;
+        tma_load_2d(base, &maps.r[a0], bx0, by0, bar);
+        tma_load_2d(base + ABOX, &maps.P[cur][a0], bx0, by0, bar);
+        tma_load_2d(base + 2 * ABOX, &maps.invd[a0], bx0, by0, bar);
+      };
+      const int G = gridDim.x;
+      int tk = blockIdx.x, k = 0;
+      unsigned pend = 0;
+#pragma unroll
+      for (int j = 0; j < NST - 1; ++j) {
+        const int tj = tk + j * G;
+        if (tj < ntask) {
+          if (tid == 0) issue(tj, j);
+          pend |= 1u << j;
+        }
+      }
+      bool tma_ok = true;
+      for (; tk < ntask; tk += G, ++k) {
+        const int s = k % NST;
+        {
+          const int tn = tk + (NST - 1) * G, sn = (k + NST - 1) % NST;
+          if (tn < ntask) {
+            if (tid == 0) issue(tn, sn);
+            pend |= 1u << sn;
+          }
+        }
+        const int w = tk / tiles, tt = tk - w * tiles;
+        int a0 = 0;
+#pragma unroll
+        for (int kk = 0; kk < L; ++kk) if (kk == w) a0 = alist[kk];
+        const int x0 = (tt % sp.tiles_x) * TX, y0 = (tt / sp.tiles_x) * TY;
+        const int gx = x0 + lx;
+        const TT* TE = static_cast<const TT*>(ip.TElo[a0]);
+        const TT* TN = static_cast<const TT*>(ip.TNlo[a0]);
+        float te[CPT], tw[CPT], tn[CPT], ts[CPT], dc[CPT];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          const int gy = y0 + ly + RPT * j;
+          const long long i = (long long)gy * pitch + gx;
+          te[j] = tw[j] = tn[j] = ts[j] = dc[j] = 0.f;
+          if (gx < nx && gy < ny) {
+            te[j] = tload(TE, i);
+            tn[j] = tload(TN, i);
+            if (gx > 0) tw[j] = tload(TE, i - 1);
+            if (gy > 0) ts[j] = tload(TN, i - pitch);
+            dc[j] = (float)dcell(sp, a0, i);
+          }
+        }
+        if (!mbar_wait(sm.bar + s, (phb >> s) & 1u, sp.spin_limit)) {
+          if (tid == 0) grid_raise_abort(irbar(sp), (int)MC_E_TIMEOUT);
+          tma_ok = false;
+          break;
+        }
+        phb ^= 1u << s;
+        pend &= ~(1u << s);
+        const float* base = sm.box + (size_t)s * 3 * ABOX;
+        const float bt = (float)beta[a0];
+        for (int e = tid; e < PN; e += NT) {
+          const int ry = e / PX, rx = e - ry * PX;
+          const int bidx = ry * BX + rx + (HOFF - 1);
+          sm.pn[e] = base[2 * ABOX + bidx] * base[bidx] + bt * base[ABOX + bidx];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          const int lyj = ly + RPT * j;
+          const int gy = y0 + lyj;
+          if (gx >= nx || gy >= ny) continue;
+          const long long i = (long long)gy * pitch + gx;
+          const int c = (lyj + 1) * PX + lx + 1;
+          const float pc = sm.pn[c];
+          const float qv = dc[j] * pc + te[j] * (pc - sm.pn[c + 1]) + tw[j] * (pc - sm.pn[c - 1]) +
+                           tn[j] * (pc - sm.pn[c + PX]) + ts[j] * (pc - sm.pn[c - PX]);
+          ip.P32[cur ^ 1][a0][i] = pc;
+          ip.q32[a0][i] = qv;
+#pragma unroll
+          for (int kk = 0; kk < L; ++kk) if (kk == a0) pq[kk] += (double)(pc * qv);
+        }
+        __syncthreads();
+      }
+      if (!tma_ok) {
+        for (int st = 0; st < NST; ++st)
+          if (pend & (1u << st)) mbar_wait(sm.bar + st, (phb >> st) & 1u, 1LL << 24);
+        return false;
+      }
+      store_part<L>(pq, sm.red, sp.partials, slot);
+      if (!gsync(sp)) return false;
+      double pqt[L];
+      sum_part<L>(sp.partials, slot, sm.res, pqt);
+      slot ^= 1;
+      float alpha[L];
+      bool brk = false;
+#pragma unroll
+      for (int a = 0; a < L; ++a) {
+        alpha[a] = 0.f;
+        if (act & (1u << a)) {
+          if (!(pqt[a] > 0.0) || !isfinite(pqt[a])) brk = true;
+          else alpha[a] = (float)(rz[a] / pqt[a]);
+        }
+      }
+      if (brk) break;  // FP32 breakdown: keep what the sweep reached
+      double acc3[2 * L];
+#pragma unroll
+      for (int kk = 0; kk < 2 * L; ++kk) acc3[kk] = 0.0;
+      const long long Np4 = Np >> 2;
+#pragma unroll
+      for (int a = 0; a < L; ++a) {
+        if (!(act & (1u << a))) continue;
+        const float al = alpha[a];
+        float4* d = reinterpret_cast<float4*>(ip.d32[a]);
+        float4* r = reinterpret_cast<float4*>(ip.r32[a]);
+        const float4* Pn = reinterpret_cast<const float4*>(ip.P32[cur ^ 1][a]);
+        const float4* qq = reinterpret_cast<const float4*>(ip.q32[a]);
+        const float4* iv = reinterpret_cast<const float4*>(ip.invd32[a]);
+        float srr = 0.f, srz = 0.f;
+#pragma unroll 2
+        for (long long j = gtid; j < Np4; j += gs) {
+          const float4 r0 = __ldcg(r + j), qv = __ldcg(qq + j), dv = __ldcg(d + j),
+                       pv = __ldcg(Pn + j), iw = __ldg(iv + j);
+          float4 rn, dn;
+          rn.x = r0.x - al * qv.x; rn.y = r0.y - al * qv.y;
+          rn.z = r0.z - al * qv.z; rn.w = r0.w - al * qv.w;
+          dn.x = dv.x + al * pv.x; dn.y = dv.y + al * pv.y;
+          dn.z = dv.z + al * pv.z; dn.w = dv.w + al * pv.w;
+          d[j] = dn;
+          r[j] = rn;
+          srr += rn.x * rn.x + rn.y * rn.y + rn.z * rn.z + rn.w * rn.w;
+          srz += rn.x * (iw.x * rn.x) + rn.y * (iw.y * rn.y) + rn.z * (iw.z * rn.z) +
+                 rn.w * (iw.w * rn.w);
+        }
+        acc3[a] += (double)srr;
+        acc3[L + a] += (double)srz;
+      }
+      store_part<2 * L>(acc3, sm.red, sp.partials, slot);
+      if (!gsync(sp)) return false;
+      double t3[2 * L];
+      sum_part<2 * L>(sp.partials, slot, sm.res, t3);
+      slot ^= 1;
+      ++it;
+#pragma unroll
+      for (int a = 0; a < L; ++a) {
+        if (!(act & (1u << a))) continue;
+        rr[a] = t3[a];
+        const double rzn = t3[L + a];
+        beta[a] = rzn / rz[a];
+        rz[a] = rzn;
+        its[a] += 1;
+        if (!(rr[a] > in2 * rr0[a]) || !isfinite(rr[a])) act &= ~(1u << a);
+        // FP32 stagnation: no decrease at all over 512 iterations (CG residual
+        // norms are not monotone, so only a flat stretch counts); the outer
+        // FP64 sweep takes over from what was reached
+        if ((it & 511) == 0) {
+          if (!(rr[a] < rck[a])) act &= ~(1u << a);
+          rck[a] = rr[a];
+        }
+      }
+      cur ^= 1;
+    }
+    // ---- 4. x += d (FP64) -------------------------------------------------------
+#pragma unroll
+    for (int a = 0; a < L; ++a) {
+      if (!(active & (1u << a))) continue;
+      for (long long i = gtid; i < Np; i += gs) sp.p[a][i] = __ldcg(sp.p[a] + i) + (double)__ldcg(ip.d32[a] + i);
+    }
+    if (!gsync(sp)) return false;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+#pragma unroll
+    for (int a = 0; a < L; ++a) {
+      if (!(mask & (1u << a))) continue;
+      sp.iters[a] += its[a];
+      if (its[a] > sp.max_iters[a]) sp.max_iters[a] = its[a];
+    }
+    atomicAdd(ip.ir_sweeps, sweeps);
+  }
+  return gsync(sp);
+}
+
+template <int L, typename TT>
+__global__ void __launch_bounds__(NT, 1)
+    ir_step_kernel(const __grid_constant__ IrParams ip, const __grid_constant__ TmaMaps maps) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  Sm sm;
+  sm.box = reinterpret_cast<float*>(base);
+  sm.pn = sm.box + NST * 3 * ABOX;
+  sm.red = reinterpret_cast<double*>(sm.pn + ((PN + 1) / 2) * 2);
+  sm.res = sm.red + (NT / 32) * KM;
+  sm.bar = reinterpret_cast<uint64_t*>(sm.res + KM);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) mbar_init(sm.bar + s, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phb = 0u;
+  int slot = 0;
+  const StepParams& sp = ip.sp;
+  const long long gtid = (long long)blockIdx.x * NT + threadIdx.x;
+  const long long gs = (long long)gridDim.x * NT;
+  int done = 0;
+  bool ok = true;
+  for (int step = 0; step < sp.nsteps && ok; ++step) {
+    for (int a = 0; a < L; ++a)
+      for (long long i = gtid; i < sp.Np; i += gs) sp.pprev[a][i] = __ldcg(sp.p[a] + i);
+    if (!gsync(sp)) { ok = false; break; }
+    if (sp.scheme == MC_SCHEME_D) {
+      ok = ir_solve<L, TT>(ip, maps, (1u << L) - 1u, sm, phb, slot);
+    } else {
+      for (int k = 0; k < L && ok; ++k) {
+        const int a = sp.scheme == MC_SCHEME_U ? L - 1 - k : k;
+        ok = ir_solve<L, TT>(ip, maps, 1u << a, sm, phb, slot);
+      }
+    }
+    if (ok) ++done;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sp.steps_done = done;
+}
+
+template <int L, typename TT>
+size_t ir_smem() {
+  return (size_t)NST * 3 * ABOX * 4 + (size_t)((PN + 1) / 2) * 2 * 4 +
+         (size_t)((NT / 32) * KM + KM) * 8 + NST * 8 + 128;
+}
+
+struct IKInfo {
+  void* fn;
+  size_t smem;
+};
+
+template <int L, typename TT>
+IKInfo iinfo() {
+  return IKInfo{(void*)ir_step_kernel<L, TT>, ir_smem<L, TT>()};
+}
+
+IKInfo ipick(int L, bool bf16) {
+  if (bf16) {
+    switch (L) {
+      case 1: return iinfo<1, __nv_bfloat16>();
+      case 2: return iinfo<2, __nv_bfloat16>();
+      case 3: return iinfo<3, __nv_bfloat16>();
+      default: return iinfo<4, __nv_bfloat16>();
+    }
+  }
+  switch (L) {
+    case 1: return iinfo<1, float>();
+    case 2: return iinfo<2, float>();
+    case 3: return iinfo<3, float>();
+    default: return iinfo<4, float>();
+  }
+}
+
+__global__ void lo_copy_kernel(long long Np, const double* TE, const double* TN, const double* invd,
+                               void* TElo, void* TNlo, float* invd32, int bf16) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (bf16) {
+      static_cast<__nv_bfloat16*>(TElo)[i] = __double2bfloat16(TE[i]);
+      static_cast<__nv_bfloat16*>(TNlo)[i] = __double2bfloat16(TN[i]);
+    } else {
+      static_cast<float*>(TElo)[i] = (float)TE[i];
+      static_cast<float*>(TNlo)[i] = (float)TN[i];
+    }
+    invd32[i] = (float)invd[i];
+  }
+}
+
+}  // namespace
+
+int mc_ir_max_blocks(int L, bool bf16, int num_sms) {
+  IKInfo k = ipick(L, bf16);
+  if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem) != cudaSuccess)
+    return 0;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k.fn, NT, k.smem) != cudaSuccess) return 0;
+  return per * num_sms;
+}
+
+int mc_ir_box_x() { return BX; }
+int mc_ir_box_y() { return BY; }
+
+cudaError_t mc_ir_prepare(mc_ctx* ctx, int bf16) {
+  const size_t fb4 = (size_t)ctx->Np * 4;
+  const size_t tb = bf16 ? (size_t)ctx->Np * 2 : fb4;
+  cudaError_t e;
+  if (ctx->lo_kind != 1 + bf16) {
+    for (int a = 0; a < ctx->L; ++a) {
+      if (!ctx->r32[a]) {
+        if ((e = mc_alloc(ctx, (void**)&ctx->r32[a], fb4)) != cudaSuccess) return e;
+        if ((e = mc_alloc(ctx, (void**)&ctx->P32[0][a], fb4)) != cudaSuccess) return e;
+        if ((e = mc_alloc(ctx, (void**)&ctx->P32[1][a], fb4)) != cudaSuccess) return e;
+        if ((e = mc_alloc(ctx, (void**)&ctx->q32[a], fb4)) != cudaSuccess) return e;
+        if ((e = mc_alloc(ctx, (void**)&ctx->d32[a], fb4)) != cudaSuccess) return e;
+        if ((e = mc_alloc(ctx, (void**)&ctx->invd32[a], fb4)) != cudaSuccess) return e;
+        if ((e = mc_alloc(ctx, (void**)&ctx->TElo32[a], fb4)) != cudaSuccess) return e;
+        if ((e = mc_alloc(ctx, (void**)&ctx->TNlo32[a], fb4)) != cudaSuccess) return e;
+      }
+      // bf16 copies live in the first half of the FP32 buffers
+      lo_copy_kernel<<<1024, 256, 0, ctx->stream>>>(ctx->Np, ctx->TE[a], ctx->TN[a], ctx->invd[a],
+                                                    ctx->TElo32[a], ctx->TNlo32[a], ctx->invd32[a], bf16);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      const int bx = BX, by = BY;
+      if ((e = mc_encode_map(&ctx->maps32.r[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->r32[a], ctx->nx,
+                             ctx->ny, ctx->pitch, bx, by)) != cudaSuccess) return e;
+      if ((e = mc_encode_map(&ctx->maps32.P[0][a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->P32[0][a],
+                             ctx->nx, ctx->ny, ctx->pitch, bx, by)) != cudaSuccess) return e;
+      if ((e = mc_encode_map(&ctx->maps32.P[1][a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->P32[1][a],
+                             ctx->nx, ctx->ny, ctx->pitch, bx, by)) != cudaSuccess) return e;
+      if ((e = mc_encode_map(&ctx->maps32.invd[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->invd32[a],
+                             ctx->nx, ctx->ny, ctx->pitch, bx, by)) != cudaSuccess) return e;
+    }
+    ctx->lo_kind = 1 + bf16;
+  }
+  (void)tb;
+  return cudaSuccess;
+}
+
+cudaError_t mc_launch_ir(mc_ctx* ctx, const StepParams& sp_in, int bf16, int blocks) {
+  IrParams ip;
+  memset(&ip, 0, sizeof(ip));
+  ip.sp = sp_in;
+  ip.sp.tiles_x = (sp_in.nx + TX - 1) / TX;
+  ip.sp.tiles_y = (sp_in.ny + TY - 1) / TY;
+  for (int a = 0; a < ctx->L; ++a) {
+    ip.r32[a] = ctx->r32[a];
+    ip.P32[0][a] = ctx->P32[0][a];
+    ip.P32[1][a] = ctx->P32[1][a];
+    ip.q32[a] = ctx->q32[a];
+    ip.d32[a] = ctx->d32[a];
+    ip.invd32[a] = ctx->invd32[a];
+    ip.TElo[a] = ctx->TElo32[a];
+    ip.TNlo[a] = ctx->TNlo32[a];
+  }
+  ip.inner_rtol = ctx->opts.inner_rtol;
+  ip.ir_max = ctx->opts.ir_max;
+  ip.ir_sweeps = ctx->dsweeps;
+  IKInfo k = ipick(ctx->L, bf16 != 0);
+  cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&ip, &ctx->maps32};
+  return cudaLaunchCooperativeKernel(k.fn, dim3(blocks), dim3(NT), args, k.smem, ctx->stream);
+}

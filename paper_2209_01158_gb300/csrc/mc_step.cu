@@ -14,9 +14,9 @@
 // row). The PCG warm-starts from p^{n-1} and updates p in place.
 //
 // PCG iteration = two phases separated by grid barriers:
-//   A (stencil): per 64 x 8 tile, TMA brings the halo boxes of r, P_old and
+//   A (stencil): per 64 x 16 tile, TMA brings the halo boxes of r, P_old and
 //     invd into shared memory (a ring of up to 6 stages: the next tiles'
-//     boxes load while this one computes); P_new = invd*r + beta*P_old on the 66 x 10
+//     boxes load while this one computes); P_new = invd*r + beta*P_old on the 66 x 18
 //     halo region, then q = A P_new on the tile and <P_new, q>.
 //   B (pointwise, vectorised): x += alpha P_new, r -= alpha q, <r, r>,
 //     <r, invd r>.
@@ -34,21 +34,23 @@
 namespace {
 
 constexpr int TX = 64;          // stencil tile width (cells along x)
-constexpr int TY = 8;           // stencil tile height
+constexpr int TY = 16;          // stencil tile height
 constexpr int HOFF = 2;         // box starts 2 doubles (16 B) left of the tile
 constexpr int BX = TX + 2 * HOFF;   // 68: box width (doubles), 544 B rows
-constexpr int BY = TY + 2;          // 10: box height
-constexpr int ABOX = 688;       // box slot in doubles (5504 B, 128-B multiple)
+constexpr int BY = TY + 2;          // 18: box height
+constexpr int ABOX = 1232;      // box slot in doubles (9856 B, 128-B multiple)
 constexpr uint32_t BOX_BYTES = BX * BY * 8;
 constexpr int PX = TX + 2;      // 66: P_new halo region width
-constexpr int PN = PX * BY;     // 660 cells
+constexpr int PN = PX * BY;     // 1188 cells
 constexpr int NT = 512;         // threads per CTA
+constexpr int RPT = NT / TX;    // 8: tile rows covered by one pass of the CTA
+constexpr int CPT = TY / RPT;   // 2: own cells per thread
 constexpr int KMAX = 4 * MCL;   // partial-sum quantities per slot
 
 // TMA pipeline depth: enough boxes in flight per SM to cover the DRAM
 // latency (Little's law: ~64 KB per SM), within 227 KB of shared memory.
 __host__ __device__ constexpr int nstage(int L, bool coupled) {
-  return !coupled ? 6 : (L <= 1 ? 6 : (L == 2 ? 4 : 3));
+  return !coupled ? 6 : (L <= 1 ? 6 : (L == 2 ? 3 : (L == 3 ? 2 : 1)));
 }
 
 __device__ __forceinline__ double ldc(const double* p) { return __ldcg(p); }
@@ -229,7 +231,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
   for (int a = 0; a < L; ++a) my_iters[a] = 0;
 
   const int tiles = sp.tiles_x * sp.tiles_y;
-  const int lx = tid % TX, ly = tid / TX;  // own cell in the tile (NT == TX * TY)
+  const int lx = tid % TX, ly = tid / TX;  // own cells (lx, ly + RPT * j), j < CPT
   while (active) {
     if (it >= sp.max_iter) {
       if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_NOCONV);
@@ -304,21 +306,23 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       }
       const int x0 = (tt % sp.tiles_x) * TX;
       const int y0 = (tt / sp.tiles_x) * TY;
-      const int gx = x0 + lx, gy = y0 + ly;
-      const bool inside = gx < nx && gy < ny;
-      const long long i = (long long)gy * pitch + gx;
-      // read-only coefficients of the own cell, fetched while TMA lands
-      double te[NL], tw[NL], tn[NL], ts[NL], dc[NL];
+      const int gx = x0 + lx;
+      // read-only coefficients of the own cells, fetched while TMA lands
+      // (decoupled tiles; the coupled tile loads them in the compute loop)
+      double te[CPT], tw[CPT], tn[CPT], ts[CPT], dc[CPT];
+      if (!COUPLED) {
 #pragma unroll
-      for (int l = 0; l < NL; ++l) {
-        const int a = COUPLED ? l : a0;
-        te[l] = tw[l] = tn[l] = ts[l] = dc[l] = 0.0;
-        if (inside) {
-          te[l] = ldr(sp.TE[a] + i);
-          tn[l] = ldr(sp.TN[a] + i);
-          if (gx > 0) tw[l] = ldr(sp.TE[a] + i - 1);
-          if (gy > 0) ts[l] = ldr(sp.TN[a] + i - pitch);
-          dc[l] = diagc(sp, a, i);
+        for (int j = 0; j < CPT; ++j) {
+          const int gy = y0 + ly + RPT * j;
+          const long long i = (long long)gy * pitch + gx;
+          te[j] = tw[j] = tn[j] = ts[j] = dc[j] = 0.0;
+          if (gx < nx && gy < ny) {
+            te[j] = ldr(sp.TE[a0] + i);
+            tn[j] = ldr(sp.TN[a0] + i);
+            if (gx > 0) tw[j] = ldr(sp.TE[a0] + i - 1);
+            if (gy > 0) ts[j] = ldr(sp.TN[a0] + i - pitch);
+            dc[j] = diagc(sp, a0, i);
+          }
         }
       }
       if (!mbar_wait(sm.bar + s, (phb >> s) & 1u, sp.spin_limit)) {
@@ -329,7 +333,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       phb ^= 1u << s;
       pend &= ~(1u << s);
       const double* base = sm.box + (size_t)s * NARR * ABOX;
-      // P_new on the 66 x 10 halo region (box columns 1..66)
+      // P_new on the 66 x 18 halo region (box columns 1..66)
 #pragma unroll
       for (int l = 0; l < NL; ++l) {
         const int a = COUPLED ? l : a0;
@@ -345,15 +349,30 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
         }
       }
       __syncthreads();
-      if (inside) {
-        const int c = (ly + 1) * PX + lx + 1;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int lyj = ly + RPT * j;
+        const int gy = y0 + lyj;
+        if (gx >= nx || gy >= ny) continue;
+        const long long i = (long long)gy * pitch + gx;
+        const int c = (lyj + 1) * PX + lx + 1;
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
           const int a = COUPLED ? l : a0;
+          double cte, ctw, ctn, cts, cdc;
+          if (COUPLED) {
+            cte = ldr(sp.TE[a] + i);
+            ctn = ldr(sp.TN[a] + i);
+            ctw = gx > 0 ? ldr(sp.TE[a] + i - 1) : 0.0;
+            cts = gy > 0 ? ldr(sp.TN[a] + i - pitch) : 0.0;
+            cdc = diagc(sp, a, i);
+          } else {
+            cte = te[j]; ctw = tw[j]; ctn = tn[j]; cts = ts[j]; cdc = dc[j];
+          }
           const double* pn = sm.pn + l * PN;
           const double pc = pn[c];
-          double qv = dc[l] * pc + te[l] * (pc - pn[c + 1]) + tw[l] * (pc - pn[c - 1]) +
-                      tn[l] * (pc - pn[c + PX]) + ts[l] * (pc - pn[c - PX]);
+          double qv = cdc * pc + cte * (pc - pn[c + 1]) + ctw * (pc - pn[c - 1]) +
+                      ctn * (pc - pn[c + PX]) + cts * (pc - pn[c - PX]);
           if (COUPLED) {
 #pragma unroll
             for (int b = 0; b < L; ++b) {
