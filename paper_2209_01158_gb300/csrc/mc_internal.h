@@ -71,6 +71,8 @@ struct IrParams {
   const float* invd32[MCL];
   const void* TElo[MCL];         // float or bf16 transmissibilities
   const void* TNlo[MCL];
+  const float* dc32[MCL];        // FP32 copy of the per-cell diag(A0 - D), or nullptr
+  float dcf[MCL];                // its constant value otherwise
   double inner_rtol;
   int ir_max;
   int* ir_sweeps;
@@ -111,6 +113,7 @@ struct mc_ctx {
   float* invd32[MCL] = {};
   float* TElo32[MCL] = {};         // FP32 copies, or BF16 in their first half
   float* TNlo32[MCL] = {};
+  float* dc32[MCL] = {};           // FP32 per-cell diag(A0 - D) when exchange varies per cell
   int lo_kind = 0;                 // 0 none, 1 FP32, 2 BF16
   TmaMaps maps32;
   int* dsweeps = nullptr;

@@ -61,19 +61,33 @@ __device__ __forceinline__ bool gsync(const StepParams& sp) {
   return ok;
 }
 
+// CTA reductions through the (idle) TMA box area of shared memory: FP64 for
+// the refinement passes, FP32 within warps (then FP64) for the inner PCG.
 template <int NQ>
-__device__ void store_part(double (&v)[NQ], double* s_red, double* partials, int slot) {
+__device__ __forceinline__ void store_part(const double (&v)[NQ], unsigned qmask, float* box,
+                                           double* partials, int slot) {
+  cta_reduce_store<NQ, NT, KM, double>(v, qmask, reinterpret_cast<double*>(box), partials, slot);
+}
+
+template <int NQ>
+__device__ __forceinline__ void store_part_f(const float (&v)[NQ], unsigned qmask, float* box,
+                                             double* partials, int slot) {
+  cta_reduce_store<NQ, NT, KM, float>(v, qmask, box, partials, slot);
+}
+
+// Grid totals of NQ quantities into s_res (shared); all threads may read
+// s_res after the call.
+template <int NQ>
+__device__ void sum_totals(const double* partials, int slot, double* s_res) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NQ; ++k) {
-    const double s = warp_sum_d(v[k]);
-    if (lane == 0) s_red[warp * NQ + k] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < NQ) {
+  const int nb = gridDim.x;
+  for (int k = warp; k < NQ; k += NT / 32) {
+    const double* src = partials + ((size_t)slot * KM + k) * nb;
     double s = 0.0;
-    for (int w = 0; w < NT / 32; ++w) s += s_red[w * NQ + threadIdx.x];
-    partials[((size_t)slot * KM + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+#pragma unroll 4
+    for (int b = lane; b < nb; b += 32) s += __ldcg(src + b);
+    s = warp_sum_d(s);
+    if (lane == 0) s_res[k] = s;
   }
   __syncthreads();
 }
@@ -106,7 +120,19 @@ __device__ __forceinline__ double dcell(const StepParams& sp, int a, long long i
   return d ? __ldg(d + i) : sp.diagc_const[a];
 }
 
+// Per-continuum scalars of the inner PCG, kept in shared memory and updated
+// by thread 0 only: the FP64 divisions and tests run once per CTA instead of
+// once per thread (FP64 issue slots are scarce on this GPU).
+struct InnerScal {
+  double rr0[MCL], rz[MCL], rr[MCL], rck[MCL];
+  float alpha[MCL], beta[MCL];
+  int its[MCL];
+  unsigned act;
+  int brk;
+};
+
 struct Sm {
+  InnerScal* sc;
   float* box;      // [NST][3][ABOX]
   float* pn;       // [PN]
   double* red;     // [NT/32][KM]
@@ -131,9 +157,9 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
 #pragma unroll
   for (int a = 0; a < L; ++a) bb[a] = 0.0;
   unsigned active = mask;
-  int its[L];
-#pragma unroll
-  for (int a = 0; a < L; ++a) its[a] = 0;
+  if (tid == 0)
+    for (int a = 0; a < MCL; ++a) sm.sc->its[a] = 0;
+  __syncthreads();
   int sweeps = 0;
   bool ok = true;
   for (int sweep = 0; ok; ++sweep) {
@@ -176,7 +202,7 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
         acc[5 * L + a] += bv * bv;
       }
     }
-    store_part<6 * L>(acc, sm.red, sp.partials, slot);
+    store_part<6 * L>(acc, qbits(active, L, 6), sm.box, sp.partials, slot);
     if (!gsync(sp)) return false;
     double t[6 * L];
     sum_part<6 * L>(sp.partials, slot, sm.res, t);
@@ -225,25 +251,26 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
     active = inner;
     if (!active) break;
     ++sweeps;
-    store_part<2 * L>(acc2, sm.red, sp.partials, slot);
+    store_part<2 * L>(acc2, qbits(inner, L, 2), sm.box, sp.partials, slot);
     if (!gsync(sp)) return false;
-    double t2[2 * L];
-    sum_part<2 * L>(sp.partials, slot, sm.res, t2);
+    sum_totals<2 * L>(sp.partials, slot, sm.res);
     slot ^= 1;
-    double rr0[L], rz[L], beta[L], rr[L], rck[L];
-#pragma unroll
-    for (int a = 0; a < L; ++a) {
-      rr0[a] = t2[a];
-      rr[a] = t2[a];
-      rck[a] = t2[a];
-      rz[a] = t2[L + a];
-      beta[a] = 0.0;
+    InnerScal& S = *sm.sc;
+    if (tid == 0) {
+      unsigned a_act = 0;
+      for (int a = 0; a < L; ++a) {
+        S.rr0[a] = S.rr[a] = S.rck[a] = sm.res[a];
+        S.rz[a] = sm.res[L + a];
+        S.beta[a] = 0.f;
+        S.alpha[a] = 0.f;
+        if ((active & (1u << a)) && sm.res[a] > 0.0) a_act |= 1u << a;
+      }
+      S.act = a_act;
+      S.brk = 0;
     }
+    __syncthreads();
     // ---- 3. FP32 inner PCG ----------------------------------------------------
-    unsigned act = 0;
-#pragma unroll
-    for (int a = 0; a < L; ++a)
-      if ((active & (1u << a)) && rr0[a] > 0.0) act |= 1u << a;
+    unsigned act = S.act;
     int cur = 0;
     int it = 0;
     const int tiles = sp.tiles_x * sp.tiles_y;
@@ -259,9 +286,9 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
       int nact = 0;
 #pragma unroll
       for (int a = 0; a < L; ++a) if (act & (1u << a)) alist[nact++] = a;
-      double pq[L];
+      float pq[L];
 #pragma unroll
-      for (int a = 0; a < L; ++a) pq[a] = 0.0;
+      for (int a = 0; a < L; ++a) pq[a] = 0.f;
       const int ntask = nact * tiles;
       auto issue = [&](int task, int s) {
         const int w = task / tiles, tt = task - w * tiles;
@@ -318,7 +345,7 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
             tn[j] = tload(TN, i);
             if (gx > 0) tw[j] = tload(TE, i - 1);
             if (gy > 0) ts[j] = tload(TN, i - pitch);
-            dc[j] = (float)dcell(sp, a0, i);
+            dc[j] = ip.dc32[a0] ? __ldg(ip.dc32[a0] + i) : ip.dcf[a0];
           }
         }
         if (!mbar_wait(sm.bar + s, (phb >> s) & 1u, sp.spin_limit)) {
@@ -329,7 +356,7 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
         phb ^= 1u << s;
         pend &= ~(1u << s);
         const float* base = sm.box + (size_t)s * 3 * ABOX;
-        const float bt = (float)beta[a0];
+        const float bt = S.beta[a0];
         for (int e = tid; e < PN; e += NT) {
           const int ry = e / PX, rx = e - ry * PX;
           const int bidx = ry * BX + rx + (HOFF - 1);
@@ -349,7 +376,7 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
           ip.P32[cur ^ 1][a0][i] = pc;
           ip.q32[a0][i] = qv;
 #pragma unroll
-          for (int kk = 0; kk < L; ++kk) if (kk == a0) pq[kk] += (double)(pc * qv);
+          for (int kk = 0; kk < L; ++kk) if (kk == a0) pq[kk] += pc * qv;
         }
         __syncthreads();
       }
@@ -358,30 +385,32 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
           if (pend & (1u << st)) mbar_wait(sm.bar + st, (phb >> st) & 1u, 1LL << 24);
         return false;
       }
-      store_part<L>(pq, sm.red, sp.partials, slot);
+      store_part_f<L>(pq, act, sm.box, sp.partials, slot);
       if (!gsync(sp)) return false;
-      double pqt[L];
-      sum_part<L>(sp.partials, slot, sm.res, pqt);
+      sum_totals<L>(sp.partials, slot, sm.res);
       slot ^= 1;
-      float alpha[L];
-      bool brk = false;
-#pragma unroll
-      for (int a = 0; a < L; ++a) {
-        alpha[a] = 0.f;
-        if (act & (1u << a)) {
-          if (!(pqt[a] > 0.0) || !isfinite(pqt[a])) brk = true;
-          else alpha[a] = (float)(rz[a] / pqt[a]);
+      if (tid == 0) {
+        int b = 0;
+        for (int a = 0; a < L; ++a) {
+          S.alpha[a] = 0.f;
+          if (act & (1u << a)) {
+            const double pqt = sm.res[a];
+            if (!(pqt > 0.0) || !isfinite(pqt)) b = 1;
+            else S.alpha[a] = (float)(S.rz[a] / pqt);
+          }
         }
+        S.brk = b;
       }
-      if (brk) break;  // FP32 breakdown: keep what the sweep reached
-      double acc3[2 * L];
+      __syncthreads();
+      if (S.brk) break;  // FP32 breakdown: keep what the sweep reached
+      float acc3[2 * L];
 #pragma unroll
-      for (int kk = 0; kk < 2 * L; ++kk) acc3[kk] = 0.0;
+      for (int kk = 0; kk < 2 * L; ++kk) acc3[kk] = 0.f;
       const long long Np4 = Np >> 2;
 #pragma unroll
       for (int a = 0; a < L; ++a) {
         if (!(act & (1u << a))) continue;
-        const float al = alpha[a];
+        const float al = S.alpha[a];
         float4* d = reinterpret_cast<float4*>(ip.d32[a]);
         float4* r = reinterpret_cast<float4*>(ip.r32[a]);
         const float4* Pn = reinterpret_cast<const float4*>(ip.P32[cur ^ 1][a]);
@@ -403,32 +432,37 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
           srz += rn.x * (iw.x * rn.x) + rn.y * (iw.y * rn.y) + rn.z * (iw.z * rn.z) +
                  rn.w * (iw.w * rn.w);
         }
-        acc3[a] += (double)srr;
-        acc3[L + a] += (double)srz;
+        acc3[a] += srr;
+        acc3[L + a] += srz;
       }
-      store_part<2 * L>(acc3, sm.red, sp.partials, slot);
+      store_part_f<2 * L>(acc3, qbits(act, L, 2), sm.box, sp.partials, slot);
       if (!gsync(sp)) return false;
-      double t3[2 * L];
-      sum_part<2 * L>(sp.partials, slot, sm.res, t3);
+      sum_totals<2 * L>(sp.partials, slot, sm.res);
       slot ^= 1;
       ++it;
-#pragma unroll
-      for (int a = 0; a < L; ++a) {
-        if (!(act & (1u << a))) continue;
-        rr[a] = t3[a];
-        const double rzn = t3[L + a];
-        beta[a] = rzn / rz[a];
-        rz[a] = rzn;
-        its[a] += 1;
-        if (!(rr[a] > in2 * rr0[a]) || !isfinite(rr[a])) act &= ~(1u << a);
-        // FP32 stagnation: no decrease at all over 512 iterations (CG residual
-        // norms are not monotone, so only a flat stretch counts); the outer
-        // FP64 sweep takes over from what was reached
-        if ((it & 511) == 0) {
-          if (!(rr[a] < rck[a])) act &= ~(1u << a);
-          rck[a] = rr[a];
+      if (tid == 0) {
+        unsigned a_act = act;
+        for (int a = 0; a < L; ++a) {
+          if (!(act & (1u << a))) continue;
+          const double rr = sm.res[a];
+          const double rzn = sm.res[L + a];
+          S.rr[a] = rr;
+          S.beta[a] = (float)(rzn / S.rz[a]);
+          S.rz[a] = rzn;
+          S.its[a] += 1;
+          if (!(rr > in2 * S.rr0[a]) || !isfinite(rr)) a_act &= ~(1u << a);
+          // FP32 stagnation: no decrease at all over 512 iterations (CG
+          // residual norms are not monotone, so only a flat stretch counts);
+          // the outer FP64 sweep takes over from what was reached
+          if ((it & 511) == 0) {
+            if (!(rr < S.rck[a])) a_act &= ~(1u << a);
+            S.rck[a] = rr;
+          }
         }
+        S.act = a_act;
       }
+      __syncthreads();
+      act = S.act;
       cur ^= 1;
     }
     // ---- 4. x += d (FP64) -------------------------------------------------------
@@ -443,8 +477,8 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
 #pragma unroll
     for (int a = 0; a < L; ++a) {
       if (!(mask & (1u << a))) continue;
-      sp.iters[a] += its[a];
-      if (its[a] > sp.max_iters[a]) sp.max_iters[a] = its[a];
+      sp.iters[a] += sm.sc->its[a];
+      if (sm.sc->its[a] > sp.max_iters[a]) sp.max_iters[a] = sm.sc->its[a];
     }
     atomicAdd(ip.ir_sweeps, sweeps);
   }
@@ -457,7 +491,9 @@ __global__ void __launch_bounds__(NT, 1)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  __shared__ InnerScal s_scal;
   Sm sm;
+  sm.sc = &s_scal;
   sm.box = reinterpret_cast<float*>(base);
   sm.pn = sm.box + NST * 3 * ABOX;
   sm.red = reinterpret_cast<double*>(sm.pn + ((PN + 1) / 2) * 2);
@@ -526,7 +562,8 @@ IKInfo ipick(int L, bool bf16) {
 }
 
 __global__ void lo_copy_kernel(long long Np, const double* TE, const double* TN, const double* invd,
-                               void* TElo, void* TNlo, float* invd32, int bf16) {
+                               const double* dc, void* TElo, void* TNlo, float* invd32,
+                               float* dc32, int bf16) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
        i += (long long)gridDim.x * blockDim.x) {
     if (bf16) {
@@ -537,6 +574,7 @@ __global__ void lo_copy_kernel(long long Np, const double* TE, const double* TN,
       static_cast<float*>(TNlo)[i] = (float)TN[i];
     }
     invd32[i] = (float)invd[i];
+    if (dc32) dc32[i] = (float)dc[i];
   }
 }
 
@@ -569,10 +607,12 @@ cudaError_t mc_ir_prepare(mc_ctx* ctx, int bf16) {
         if ((e = mc_alloc(ctx, (void**)&ctx->invd32[a], fb4)) != cudaSuccess) return e;
         if ((e = mc_alloc(ctx, (void**)&ctx->TElo32[a], fb4)) != cudaSuccess) return e;
         if ((e = mc_alloc(ctx, (void**)&ctx->TNlo32[a], fb4)) != cudaSuccess) return e;
+        if (ctx->diagc[a] && (e = mc_alloc(ctx, (void**)&ctx->dc32[a], fb4)) != cudaSuccess) return e;
       }
       // bf16 copies live in the first half of the FP32 buffers
       lo_copy_kernel<<<1024, 256, 0, ctx->stream>>>(ctx->Np, ctx->TE[a], ctx->TN[a], ctx->invd[a],
-                                                    ctx->TElo32[a], ctx->TNlo32[a], ctx->invd32[a], bf16);
+                                                    ctx->diagc[a], ctx->TElo32[a], ctx->TNlo32[a],
+                                                    ctx->invd32[a], ctx->dc32[a], bf16);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       const int bx = BX, by = BY;
       if ((e = mc_encode_map(&ctx->maps32.r[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->r32[a], ctx->nx,
@@ -605,6 +645,8 @@ cudaError_t mc_launch_ir(mc_ctx* ctx, const StepParams& sp_in, int bf16, int blo
     ip.invd32[a] = ctx->invd32[a];
     ip.TElo[a] = ctx->TElo32[a];
     ip.TNlo[a] = ctx->TNlo32[a];
+    ip.dc32[a] = ctx->dc32[a];
+    ip.dcf[a] = (float)sp_in.diagc_const[a];
   }
   ip.inner_rtol = ctx->opts.inner_rtol;
   ip.ir_max = ctx->opts.ir_max;

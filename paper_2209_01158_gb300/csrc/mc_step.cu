@@ -79,20 +79,26 @@ __device__ bool grid_sync(const StepParams& sp) {
   return ok;
 }
 
+// CTA reduction through the (idle) TMA box area of shared memory.
 template <int NQ>
-__device__ void block_store(double (&v)[NQ], double* s_red, double* partials, int slot) {
+__device__ __forceinline__ void block_store(const double (&v)[NQ], unsigned qmask, double* stage,
+                                            double* partials, int slot) {
+  cta_reduce_store<NQ, NT, KMAX, double>(v, qmask, stage, partials, slot);
+}
+
+// Grid totals of NQ quantities into s_res (shared), readable by all threads.
+template <int NQ>
+__device__ void grid_totals(const double* partials, int slot, double* s_res) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NQ; ++k) {
-    double s = warp_sum(v[k]);
-    if (lane == 0) s_red[warp * NQ + k] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < NQ) {
+  const int nb = gridDim.x;
+  for (int k = warp; k < NQ; k += nw) {
+    const double* src = partials + ((size_t)slot * KMAX + k) * nb;
     double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += s_red[w * NQ + threadIdx.x];
-    partials[((size_t)slot * KMAX + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+#pragma unroll 4
+    for (int b = lane; b < nb; b += 32) s += ldc(src + b);
+    s = warp_sum(s);
+    if (lane == 0) s_res[k] = s;
   }
   __syncthreads();
 }
@@ -138,7 +144,17 @@ __device__ __forceinline__ double stencil_flux(const StepParams& sp, int a, cons
   return s;
 }
 
+// Per-continuum PCG scalars in shared memory, updated by thread 0 only: the
+// FP64 divisions and convergence tests run once per CTA, not per thread.
+struct Scal64 {
+  double bb[MCL], rr[MCL], rz[MCL], beta[MCL], alpha[MCL];
+  int iters[MCL];
+  unsigned active;
+  int flag;  // 1 breakdown
+};
+
 struct Smem {
+  Scal64* sc;
   double* box;      // [NST stages][NARR][ABOX]
   double* pn;       // [NL][PN]
   double* red;      // [NT/32][KMAX]
@@ -194,41 +210,36 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       acc[2 * L + a] += rv * z;
     }
   }
-  block_store<3 * L>(acc, sm.red, sp.partials, 0);
+  block_store<3 * L>(acc, qbits(mask, L, 3), sm.box, sp.partials, 0);
   if (!grid_sync(sp)) return false;
-  double tot[3 * L];
-  grid_sum<3 * L>(sp.partials, 0, sm.res, tot);
-
-  double bb[L], rr[L], rz[L], beta[L];
-#pragma unroll
-  for (int a = 0; a < L; ++a) {
-    bb[a] = tot[a];
-    rr[a] = tot[L + a];
-    rz[a] = tot[2 * L + a];
-    beta[a] = 0.0;
-  }
-  if (COUPLED) {
-    double sb = 0, sr = 0, sz = 0;
-#pragma unroll
-    for (int a = 0; a < L; ++a) {
-      if (mask & (1u << a)) { sb += bb[a]; sr += rr[a]; sz += rz[a]; }
-    }
-#pragma unroll
-    for (int a = 0; a < L; ++a) { bb[a] = sb; rr[a] = sr; rz[a] = sz; }
-  }
+  grid_totals<3 * L>(sp.partials, 0, sm.res);
   const double rtol2 = sp.rtol * sp.rtol;
-  unsigned active = 0;
-#pragma unroll
-  for (int a = 0; a < L; ++a) {
-    if ((mask & (1u << a)) && rr[a] > rtol2 * bb[a]) active |= 1u << a;
+  Scal64& S = *sm.sc;
+  if (tid == 0) {
+    double sb = 0, sr = 0, sz = 0;
+    for (int a = 0; a < L; ++a) {
+      S.bb[a] = sm.res[a];
+      S.rr[a] = sm.res[L + a];
+      S.rz[a] = sm.res[2 * L + a];
+      S.beta[a] = 0.0;
+      S.alpha[a] = 0.0;
+      S.iters[a] = 0;
+      if (mask & (1u << a)) { sb += S.bb[a]; sr += S.rr[a]; sz += S.rz[a]; }
+    }
+    if (COUPLED)
+      for (int a = 0; a < L; ++a) { S.bb[a] = sb; S.rr[a] = sr; S.rz[a] = sz; }
+    unsigned act = 0;
+    for (int a = 0; a < L; ++a)
+      if ((mask & (1u << a)) && S.rr[a] > rtol2 * S.bb[a]) act |= 1u << a;
+    S.active = act;
+    S.flag = 0;
   }
+  __syncthreads();
+  unsigned active = S.active;
   int it = 0;
   int cur = 0;
   int slot = 1;
   bool ok = true;
-  int my_iters[L];
-#pragma unroll
-  for (int a = 0; a < L; ++a) my_iters[a] = 0;
 
   const int tiles = sp.tiles_x * sp.tiles_y;
   const int lx = tid % TX, ly = tid / TX;  // own cells (lx, ly + RPT * j), j < CPT
@@ -337,7 +348,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
 #pragma unroll
       for (int l = 0; l < NL; ++l) {
         const int a = COUPLED ? l : a0;
-        const double bt = beta[a];
+        const double bt = S.beta[a];
         const double* br = base + (3 * l + 0) * ABOX;
         const double* bp = base + (3 * l + 1) * ABOX;
         const double* bi = base + (3 * l + 2) * ABOX;
@@ -396,29 +407,26 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       ok = false;
       break;
     }
-    block_store<L>(pq, sm.red, sp.partials, slot);
+    block_store<L>(pq, active, sm.box, sp.partials, slot);
     if (!grid_sync(sp)) { ok = false; break; }
-    double pqt[L];
-    grid_sum<L>(sp.partials, slot, sm.res, pqt);
+    grid_totals<L>(sp.partials, slot, sm.res);
     slot ^= 1;
-    if (COUPLED) {
-      double s = 0;
-#pragma unroll
-      for (int a = 0; a < L; ++a) s += pqt[a];
-#pragma unroll
-      for (int a = 0; a < L; ++a) pqt[a] = s;
-    }
-    double alpha[L];
-    bool brk = false;
-#pragma unroll
-    for (int a = 0; a < L; ++a) {
-      alpha[a] = 0.0;
-      if (active & (1u << a)) {
-        if (!(pqt[a] > 0.0) || !isfinite(pqt[a])) brk = true;
-        else alpha[a] = rz[a] / pqt[a];
+    if (tid == 0) {
+      double pqs = 0.0;
+      for (int a = 0; a < L; ++a) pqs += sm.res[a];
+      int brk = 0;
+      for (int a = 0; a < L; ++a) {
+        S.alpha[a] = 0.0;
+        if (active & (1u << a)) {
+          const double pqt = COUPLED ? pqs : sm.res[a];
+          if (!(pqt > 0.0) || !isfinite(pqt)) brk = 1;
+          else S.alpha[a] = S.rz[a] / pqt;
+        }
       }
+      S.flag = brk;
     }
-    if (brk) {
+    __syncthreads();
+    if (S.flag) {
       if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_BREAKDOWN);
       ok = false;
       break;
@@ -431,7 +439,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
 #pragma unroll
     for (int a = 0; a < L; ++a) {
       if (!(active & (1u << a))) continue;
-      const double al = alpha[a];
+      const double al = S.alpha[a];
       double2* x = reinterpret_cast<double2*>(sp.p[a]);
       double2* r = reinterpret_cast<double2*>(sp.r[a]);
       const double2* Pn = reinterpret_cast<const double2*>(sp.P[cur ^ 1][a]);
@@ -455,34 +463,37 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
         acc2[L + a] += rv.x * (dv.x * rv.x) + rv.y * (dv.y * rv.y);
       }
     }
-    block_store<2 * L>(acc2, sm.red, sp.partials, slot);
+    block_store<2 * L>(acc2, qbits(active, L, 2), sm.box, sp.partials, slot);
     if (!grid_sync(sp)) { ok = false; break; }
-    double t2[2 * L];
-    grid_sum<2 * L>(sp.partials, slot, sm.res, t2);
+    grid_totals<2 * L>(sp.partials, slot, sm.res);
     slot ^= 1;
-    if (COUPLED) {
-      double s0 = 0, s1 = 0;
-#pragma unroll
-      for (int a = 0; a < L; ++a) { s0 += t2[a]; s1 += t2[L + a]; }
-#pragma unroll
-      for (int a = 0; a < L; ++a) { t2[a] = s0; t2[L + a] = s1; }
-    }
     ++it;
-#pragma unroll
-    for (int a = 0; a < L; ++a) {
-      if (!(active & (1u << a))) continue;
-      rr[a] = t2[a];
-      const double rzn = t2[L + a];
-      beta[a] = rzn / rz[a];
-      rz[a] = rzn;
-      my_iters[a] = it;
-      if (!(rr[a] > rtol2 * bb[a])) active &= ~(1u << a);
-      if (!isfinite(rr[a])) {
-        if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_BREAKDOWN);
-        ok = false;
+    if (tid == 0) {
+      double s0 = 0, s1 = 0;
+      for (int a = 0; a < L; ++a) { s0 += sm.res[a]; s1 += sm.res[L + a]; }
+      unsigned act = active;
+      int bad = 0;
+      for (int a = 0; a < L; ++a) {
+        if (!(active & (1u << a))) continue;
+        const double rra = COUPLED ? s0 : sm.res[a];
+        const double rzn = COUPLED ? s1 : sm.res[L + a];
+        S.rr[a] = rra;
+        S.beta[a] = rzn / S.rz[a];
+        S.rz[a] = rzn;
+        S.iters[a] = it;
+        if (!(rra > rtol2 * S.bb[a])) act &= ~(1u << a);
+        if (!isfinite(rra)) bad = 1;
       }
+      S.active = act;
+      S.flag = bad;
     }
-    if (!ok) break;
+    __syncthreads();
+    active = S.active;
+    if (S.flag) {
+      if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_BREAKDOWN);
+      ok = false;
+      break;
+    }
     cur ^= 1;
   }
   // ---- constant-mode correction --------------------------------------------
@@ -530,7 +541,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
           for (int b = a + 1; b < L; ++b) cs[L + pi++] += qab(sp, a, b, i);
       }
     }
-    block_store<NQC>(cs, sm.red, sp.partials, slot);
+    block_store<NQC>(cs, (1u << NQC) - 1u, sm.box, sp.partials, slot);
     if (!grid_sync(sp)) {
       ok = false;
     } else {
@@ -600,9 +611,9 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       if (!(mask & (1u << a))) continue;
       if (COUPLED && a != 0) continue;
       const int ka = COUPLED ? 0 : a;
-      sp.iters[ka] += my_iters[a];
-      if (my_iters[a] > sp.max_iters[ka]) sp.max_iters[ka] = my_iters[a];
-      sp.relres[ka] = bb[a] > 0 ? sqrt(rr[a] / bb[a]) : sqrt(rr[a]);
+      sp.iters[ka] += S.iters[a];
+      if (S.iters[a] > sp.max_iters[ka]) sp.max_iters[ka] = S.iters[a];
+      sp.relres[ka] = S.bb[a] > 0 ? sqrt(S.rr[a] / S.bb[a]) : sqrt(S.rr[a]);
     }
   }
   // The next solve's first pass reads p and rewrites partial slot 0: every
@@ -621,7 +632,9 @@ __global__ void __launch_bounds__(NT, 1)
   // TMA destinations need 128-B aligned slots: align the dynamic base.
   unsigned char* smem_base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  __shared__ Scal64 s_scal;
   Smem sm;
+  sm.sc = &s_scal;
   sm.box = reinterpret_cast<double*>(smem_base);
   sm.pn = sm.box + NST * NARR * ABOX;
   sm.red = sm.pn + NL * PN;
@@ -684,7 +697,7 @@ __global__ void __launch_bounds__(NT, 1)
         acc[3] += sp.tau * fabs(e);
       }
   }
-  block_store<4>(acc, sm.red, sp.partials, 0);
+  block_store<4>(acc, 0xfu, sm.box, sp.partials, 0);
   if (!grid_sync(sp)) return;
   double t[4];
   grid_sum<4>(sp.partials, 0, sm.res, t);
