@@ -99,6 +99,22 @@ def precision_4096(n=4096, seed=3, nsteps=100):
                     seed=seed)
 
 
+def _fracture_sources(ell, n, L):
+    """+1 / -1 in the fracture continuum at the fracture cells nearest to
+    (n/8, n/8) and (7n/8, 7n/8): the wells sit in fractures, as in the
+    paper's experiments (Section 5)."""
+    F = [np.zeros((n, n)) for _ in range(L)]
+    jj, ii = np.nonzero(ell > 0.0)
+    for (t, v) in ((n // 8, 1.0), ((7 * n) // 8, -1.0)):
+        if jj.size:
+            d = (ii - t) ** 2 + (jj - t) ** 2
+            k = int(np.argmin(d))
+            F[L - 1][jj[k], ii[k]] += v
+        else:
+            F[L - 1][t, t] += v
+    return F
+
+
 def fracture_instance(seed, n=None, L=None, tau=1.0 / 100, nsteps=100,
                       sizes=(128, 256, 512, 1024)):
     """One realisation with an embedded fracture continuum (the last one).
@@ -108,7 +124,8 @@ def fracture_instance(seed, n=None, L=None, tau=1.0 / 100, nsteps=100,
     field (log-normal, mean 1e2), then 20..200 random segments. Cells crossed
     by a segment get k = 1e4 in the fracture continuum, all others 1e-2; the
     fracture exchanges with every other continuum through
-    sigma_i = 10 * l_i / h, l_i the segment length inside cell i.
+    sigma_i = 10 * l_i / h, l_i the segment length inside cell i. The sources
+    are in the fracture cells nearest to (n/8, n/8) and (7n/8, 7n/8).
     """
     rng = np.random.default_rng(seed)
     if L is None:
@@ -134,7 +151,7 @@ def fracture_instance(seed, n=None, L=None, tau=1.0 / 100, nsteps=100,
         sigma = _sym(3, {(0, 1): 5.0})
         sc = {(0, 2): sig_f, (1, 2): sig_f.copy()}
     return Workload("fracture_%d_L%d_s%d" % (n, L, seed), n, n, L, k, c, sigma,
-                    tau, nsteps, _point_sources(n, L, L - 1),
+                    tau, nsteps, _fracture_sources(ell, n, L),
                     [np.zeros((n, n))] * L, sigma_cell=sc, seed=seed)
 
 
