@@ -48,6 +48,7 @@ extern "C" {
 
 typedef struct mc_ctx mc_ctx;
 typedef struct mc_nlmc mc_nlmc;
+typedef struct mc_batch mc_batch;
 
 typedef enum {
   MC_OK = 0,
@@ -73,10 +74,16 @@ typedef struct {
                           inner PCG inside FP64 iterative refinement */
   int32_t precond;     /* MC_PRECOND_JACOBI */
   int32_t max_iter;    /* PCG iterations per solve (IR forms: cap of each inner
-                          solve, further limited to 4 max(nx, ny) (>= 512);
-                          an inner solve also stops when FP32 stagnates) */
+                          solve, further limited to 16 max(nx, ny) within
+                          [2048, 16384]; an inner solve also stops when its
+                          smallest residual norm fails to halve within 2048
+                          iterations) */
   int32_t ir_max;      /* maximum refinement sweeps per solve (IR forms) */
-  double rtol;         /* stop when ||b - A x||_2 <= rtol ||b||_2 (FP64) */
+  double rtol;         /* stop when ||b - A x||_2 <= rtol ||b||_2 (FP64). IR
+                          forms also stop at the floor of refinement (an inner
+                          solve met inner_rtol but the sweep did not halve
+                          ||r||) when that floor is within 1e3 rtol ||b||;
+                          rel_residual reports what was met */
   double inner_rtol;   /* inner PCG relative residual target of each IR sweep
                           (default 1e-3) */
   int64_t spin_limit;  /* polls of a grid barrier before MC_E_TIMEOUT */
@@ -227,6 +234,82 @@ mc_status mc_nlmc_get_basis(mc_nlmc* m, int32_t block, int32_t beta, double* psi
 mc_status mc_nlmc_info(const mc_nlmc* m, int64_t* info);
 
 void mc_nlmc_destroy(mc_nlmc* m);
+
+/* ---------------- Batched precision form -------------------------------------
+ *
+ * Many independent problems (instances) of uneven grid sizes and numbers of
+ * continua stepped together by the D-, L- or U-scheme of Section 3.3 in the
+ * precision form (FP32 or BF16-transmissibility inner PCG inside FP64
+ * iterative refinement, exactly as mc_step_decoupled with that precision).
+ * Each time step of the whole batch is ONE persistent kernel launch: the
+ * co-resident CTAs form teams of `team` CTAs, and each team takes instances
+ * (largest first) from a shared counter and solves them with team-wide
+ * barriers. The launches of one mc_batch_step call are captured into a CUDA
+ * graph on first use and replayed by later calls with the same scheme,
+ * nsteps and team size.
+ *
+ * mc_batch_create -- group n contexts (from mc_setup, all on one device)
+ *   into a batch. The contexts stay owned by the caller and must outlive the
+ *   batch; their sources and state are read and written through the usual
+ *   calls (mc_set_source, mc_set_state, mc_get_state), which may be issued
+ *   between batch calls. opts: precision MC_PREC_FP32_IR or MC_PREC_BF16T_IR
+ *   (else MC_E_ARG), rtol, inner_rtol, max_iter, ir_max, spin_limit apply to
+ *   every instance (the contexts' own opts are not used by the batch);
+ *   opts->blocks caps the CTAs of the launch (0: all co-resident). The team
+ *   size starts at a heuristic (the smallest power of two for which the
+ *   largest instance's share of the work fits one team's share of the GPU).
+ *   Allocates the members' FP32 work vectors if they have none.
+ */
+mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t n, const mc_opts* opts,
+                          mc_batch** out);
+
+/* CTAs per team, 1..(CTAs of the launch); MC_E_ARG otherwise. */
+mc_status mc_batch_set_team(mc_batch* b, int32_t team);
+
+/*
+ * mc_batch_step -- nsteps steps of every instance (scheme MC_SCHEME_D, _L
+ *   or _U). Per instance and continuum the solve stops on the FP64 residual
+ *   test ||b - A x|| <= rtol ||b||. An instance whose solve fails
+ *   (MC_E_NOCONV after ir_max sweeps) is put back to the start of that step
+ *   and left there for the rest of the call; the others go on. A barrier
+ *   timeout stops the whole call (MC_E_TIMEOUT) with every instance at the
+ *   end of its last completed step. Returns the status of the first failed
+ *   instance (index order); `total` (may be NULL) gets the minimum
+ *   steps_done, that status, iteration and sweep counts summed over the
+ *   instances (max_iters: the maximum). Synchronises.
+ */
+mc_status mc_batch_step(mc_batch* b, int32_t scheme, int32_t nsteps, mc_stats* total);
+
+/* Statistics of instance i from the last mc_batch_step: steps_done, status,
+ * iters, max_iters, ir_sweeps, rel_residual of the last solve (mass_defect
+ * is 0). */
+mc_status mc_batch_instance_stats(mc_batch* b, int32_t i, mc_stats* s);
+
+/*
+ * mc_batch_autotune -- choose the team size by timing one batched step per
+ *   candidate (after one untimed step), with CUDA events; every trial step is
+ *   undone, so the instances' states are unchanged. candidates: ncand team
+ *   sizes, or NULL for 1, 2, 4, ... up to the CTAs of the launch. ms (may be
+ *   NULL): ncand times in milliseconds (-1 when not timed). cache_path (may be
+ *   NULL): a JSON file mapping a key (device, precision, scheme, CTAs, and the
+ *   batch's sorted list of instance shapes) to the chosen team size; a hit
+ *   skips the timing, a miss appends the result. The chosen size is kept for
+ *   later mc_batch_step calls and returned in *best_team (may be NULL).
+ */
+mc_status mc_batch_autotune(mc_batch* b, int32_t scheme, const int32_t* candidates,
+                            int32_t ncand, const char* cache_path, int32_t* best_team,
+                            double* ms);
+
+/* info[0..7] = instances, team size, teams, CTAs per launch, whether the last
+ * step ran as a graph replay (1/0), whether the team size came from the tuner
+ * cache (1/0), continuum cells summed over the instances, device bytes held
+ * by the batch itself. */
+mc_status mc_batch_info(const mc_batch* b, int64_t* info);
+
+/* Last error text of b (or of the last failed mc_batch_create when NULL). */
+const char* mc_batch_last_error(const mc_batch* b);
+
+void mc_batch_destroy(mc_batch* b);
 
 /*
  * mc_step_single_noalloc -- nsteps backward-Euler steps of ONE continuum,

@@ -370,3 +370,73 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Owning wrapper of an mc_batch over a list of Context objects (which must
+    stay open while the batch lives)."""
+
+    def __init__(self, contexts, opts, team=None):
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c.handle.value for c in self.contexts])
+        h = C.c_void_p()
+        st = _lib().mc_batch_create(arr, len(self.contexts), C.byref(opts), C.byref(h))
+        if st != N.MC_OK:
+            raise MCError(st, _lib().mc_batch_last_error(None).decode())
+        self._h = h
+        if team is not None:
+            self.set_team(team)
+
+    def _check(self, st):
+        if st != N.MC_OK:
+            raise MCError(st, _lib().mc_batch_last_error(self._h).decode())
+
+    def set_team(self, team):
+        self._check(_lib().mc_batch_set_team(self._h, int(team)))
+
+    def step(self, scheme="D", nsteps=1, check=True):
+        sc = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+        s = N.mc_stats()
+        st = _lib().mc_batch_step(self._h, int(sc), int(nsteps), C.byref(s))
+        d = _stats_dict(s, MC_MAX_CONTINUA)
+        d["return"] = st
+        if check:
+            self._check(st)
+        return d
+
+    def instance_stats(self, i):
+        s = N.mc_stats()
+        self._check(_lib().mc_batch_instance_stats(self._h, int(i), C.byref(s)))
+        return _stats_dict(s, self.contexts[i].L)
+
+    def autotune(self, scheme="D", candidates=None, cache_path=None):
+        sc = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+        cand = None
+        n = 0
+        ms = None
+        if candidates is not None:
+            n = len(candidates)
+            cand = (C.c_int32 * n)(*[int(x) for x in candidates])
+            ms = np.full(n, -1.0)
+        best = C.c_int32()
+        self._check(_lib().mc_batch_autotune(
+            self._h, int(sc), cand, n, cache_path.encode() if cache_path else None,
+            C.byref(best), ms.ctypes.data_as(N.dp) if ms is not None else None))
+        return best.value, (list(ms) if ms is not None else None)
+
+    def info(self):
+        v = (C.c_int64 * 8)()
+        self._check(_lib().mc_batch_info(self._h, v))
+        return {"n": v[0], "team": v[1], "teams": v[2], "ctas": v[3], "graph": v[4],
+                "from_cache": v[5], "continuum_cells": v[6], "device_bytes": v[7]}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().mc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

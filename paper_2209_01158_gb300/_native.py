@@ -70,6 +70,16 @@ SIGNATURES = {
     "mc_nlmc_get_basis": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, dp]),
     "mc_nlmc_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "mc_nlmc_destroy": (None, [C.c_void_p]),
+    "mc_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(mc_opts),
+                                  C.POINTER(C.c_void_p)]),
+    "mc_batch_set_team": (C.c_int, [C.c_void_p, C.c_int32]),
+    "mc_batch_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(mc_stats)]),
+    "mc_batch_instance_stats": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(mc_stats)]),
+    "mc_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_int32,
+                                    C.c_char_p, C.POINTER(C.c_int32), dp]),
+    "mc_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "mc_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "mc_batch_destroy": (None, [C.c_void_p]),
     "mc_destroy": (None, [C.c_void_p]),
     "mc_last_error": (C.c_char_p, [C.c_void_p]),
     "mc_status_string": (C.c_char_p, [C.c_int]),

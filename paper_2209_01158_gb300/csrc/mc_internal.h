@@ -76,6 +76,40 @@ struct IrParams {
   double inner_rtol;
   int ir_max;
   int* ir_sweeps;
+  unsigned* abort_word;          // raised by a timed-out barrier; every barrier polls it
+};
+
+// Per-instance record of the batched precision form (device memory).
+struct BatchInst {
+  int status;                    // mc_status of the instance (0 = OK)
+  int steps_done;                // steps completed since the last reset
+  int ir_sweeps;
+  int busy;                      // 1 while a team holds the instance mid-step
+  long long iters[MCL];
+  int max_iters[MCL];
+  double relres[MCL];            // ||r|| / ||b|| at the end of the last solve
+};
+
+// Everything the batched persistent kernel needs, passed by value. The grid
+// is split into `teams` teams of `team` CTAs; each team takes instances from
+// a shared counter in the order `order` (largest first) and runs the
+// precision-form step of that instance with team-scoped barriers.
+struct BatchParams {
+  const IrParams* inst;          // [n] (device), per-instance pointers and constants
+  const TmaMaps* maps;           // [n] (device)
+  const int* order;              // [n] instance indices, largest first
+  BatchInst* st;                 // [n]
+  int n;
+  int team, teams;
+  int scheme;
+  double rtol;
+  double inner_rtol;
+  int max_iter, ir_max;
+  long long spin_limit;
+  unsigned* ctrl;                // [0] queue; team t: u64 barrier count at 32(t+1),
+                                 // ticket at 32(t+1)+4 (zeroed before each launch)
+  unsigned* abort_word;          // zeroed before each batched call
+  double* partials;              // team t: [2 slots][MC_KMAX_ALLOC][team] from t*2*KM*team
 };
 
 struct mc_ctx {
@@ -150,6 +184,13 @@ int mc_step_box_y();
 int mc_ir_max_blocks(int L, bool bf16, int num_sms);
 cudaError_t mc_ir_prepare(mc_ctx* ctx, int bf16);
 cudaError_t mc_launch_ir(mc_ctx* ctx, const StepParams& sp, int bf16, int blocks);
+// IrParams of a prepared context (mc_ir_prepare done) around StepParams sp.
+void mc_ir_fill(const mc_ctx* ctx, const StepParams& sp, IrParams* ip);
+// Batched form: co-resident CTAs of the batched kernel, and one launch (one
+// time step of every instance) queued on `stream` (cooperative attribute set,
+// so it may be captured into a CUDA graph).
+int mc_ir_batch_max_blocks(bool bf16, int num_sms);
+cudaError_t mc_launch_ir_batch(const BatchParams& bp, int bf16, int blocks, cudaStream_t stream);
 
 // Encode a 2-D tiled tensor map (x innermost) over a pitched array.
 cudaError_t mc_encode_map(CUtensorMap* map, CUtensorMapDataType dtype, int esize, void* base,

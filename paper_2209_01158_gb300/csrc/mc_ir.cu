@@ -10,7 +10,14 @@
 //      (1^T D = 0), so x += c, r -= c diag(A0 - D) with
 //      c = 1^T r / 1^T diag(A0 - D); the FP32 solve cannot resolve this
 //      near-null mode, the FP64 shift does;
-//   3. stop when ||r|| <= rtol ||b|| (FP64);
+//   3. stop when ||r|| <= rtol ||b|| (FP64), or when refinement has reached
+//      its floor: the last inner solve met its own target but the sweep did
+//      not halve ||r|| (the rule LAPACK's refinement uses: stop once the
+//      backward error no longer halves), with ||r|| already within
+//      1e3 rtol ||b||. On fracture continua (k 1e4 on thin networks, 1e-2
+//      around them) FP32-corrected refinement levels off near 1e-11 ||b||
+//      while the error is ~1e-13: the FP32 corrections carry large
+//      near-null components that the operator maps to small residuals;
 //   4. FP32 PCG on A d = r (transmissibilities stored FP32 or BF16, FP32
 //      vectors, Jacobi), to a relative residual inner_rtol; the dot products
 //      are summed per thread in FP32 and then across the grid in FP64;
@@ -46,17 +53,25 @@ __device__ __forceinline__ float tload(const __nv_bfloat16* p, long long i) {
   return __bfloat162float(p[i]);
 }
 
-__device__ __forceinline__ GridBar irbar(const StepParams& sp) {
+// The CTAs that cooperate on one solve: the whole grid, or one team of the
+// batched kernel. rank/size replace blockIdx.x/gridDim.x everywhere below.
+struct Team {
+  int rank, size;
+};
+
+__device__ __forceinline__ GridBar irbar(const IrParams& ip, const Team& tm) {
+  const StepParams& sp = ip.sp;
   GridBar g;
   g.count = reinterpret_cast<unsigned long long*>(sp.bar_count);
-  g.abort_word = sp.bar_gen + 32;
+  g.abort_word = ip.abort_word;
   g.status = sp.status;
   g.spin_limit = sp.spin_limit;
+  g.nparts = (unsigned)tm.size;
   return g;
 }
 
-__device__ __forceinline__ bool gsync(const StepParams& sp) {
-  const bool ok = grid_barrier(irbar(sp));
+__device__ __forceinline__ bool gsync(const IrParams& ip, const Team& tm) {
+  const bool ok = grid_barrier(irbar(ip, tm));
   if (threadIdx.x == 0) fence_proxy_async();
   return ok;
 }
@@ -65,22 +80,23 @@ __device__ __forceinline__ bool gsync(const StepParams& sp) {
 // the refinement passes, FP32 within warps (then FP64) for the inner PCG.
 template <int NQ>
 __device__ __forceinline__ void store_part(const double (&v)[NQ], unsigned qmask, float* box,
-                                           double* partials, int slot) {
-  cta_reduce_store<NQ, NT, KM, double>(v, qmask, reinterpret_cast<double*>(box), partials, slot);
+                                           double* partials, int slot, const Team& tm) {
+  cta_reduce_store<NQ, NT, KM, double>(v, qmask, reinterpret_cast<double*>(box), partials, slot,
+                                       tm.size, tm.rank);
 }
 
 template <int NQ>
 __device__ __forceinline__ void store_part_f(const float (&v)[NQ], unsigned qmask, float* box,
-                                             double* partials, int slot) {
-  cta_reduce_store<NQ, NT, KM, float>(v, qmask, box, partials, slot);
+                                             double* partials, int slot, const Team& tm) {
+  cta_reduce_store<NQ, NT, KM, float>(v, qmask, box, partials, slot, tm.size, tm.rank);
 }
 
 // Grid totals of NQ quantities into s_res (shared); all threads may read
 // s_res after the call.
 template <int NQ>
-__device__ void sum_totals(const double* partials, int slot, double* s_res) {
+__device__ void sum_totals(const double* partials, int slot, double* s_res, const Team& tm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nb = gridDim.x;
+  const int nb = tm.size;
   for (int k = warp; k < NQ; k += NT / 32) {
     const double* src = partials + ((size_t)slot * KM + k) * nb;
     double s = 0.0;
@@ -93,9 +109,10 @@ __device__ void sum_totals(const double* partials, int slot, double* s_res) {
 }
 
 template <int NQ>
-__device__ void sum_part(const double* partials, int slot, double* s_res, double (&out)[NQ]) {
+__device__ void sum_part(const double* partials, int slot, double* s_res, double (&out)[NQ],
+                         const Team& tm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nb = gridDim.x;
+  const int nb = tm.size;
   for (int k = warp; k < NQ; k += NT / 32) {
     const double* src = partials + ((size_t)slot * KM + k) * nb;
     double s = 0.0;
@@ -124,14 +141,16 @@ __device__ __forceinline__ double dcell(const StepParams& sp, int a, long long i
 // by thread 0 only: the FP64 divisions and tests run once per CTA instead of
 // once per thread (FP64 issue slots are scarce on this GPU).
 struct InnerScal {
-  double rr0[MCL], rz[MCL], rr[MCL], rck[MCL];
+  double rr0[MCL], rz[MCL], rr[MCL], rmin[MCL], rck[MCL];
   float alpha[MCL], beta[MCL];
   int its[MCL];
   unsigned act;
+  unsigned iok;    // continua whose last inner solve met inner_rtol
   int brk;
 };
 
 struct Sm {
+  Team team;
   InnerScal* sc;
   float* box;      // [NST][3][ABOX]
   float* pn;       // [PN]
@@ -148,15 +167,17 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
   const int nx = sp.nx, ny = sp.ny, pitch = sp.pitch;
   const long long Np = sp.Np;
   const int tid = threadIdx.x;
-  const long long gtid = (long long)blockIdx.x * NT + tid;
-  const long long gs = (long long)gridDim.x * NT;
+  const Team tm = sm.team;
+  const long long gtid = (long long)tm.rank * NT + tid;
+  const long long gs = (long long)tm.size * NT;
   const bool lag_prev = sp.scheme == MC_SCHEME_D;
   const double rtol2 = sp.rtol * sp.rtol;
   const double in2 = ip.inner_rtol * ip.inner_rtol;
-  double bb[L];
+  double bb[L], rr_prev[L], rr_last[L];
 #pragma unroll
-  for (int a = 0; a < L; ++a) bb[a] = 0.0;
+  for (int a = 0; a < L; ++a) bb[a] = rr_prev[a] = rr_last[a] = 0.0;
   unsigned active = mask;
+  unsigned iok = 0;
   if (tid == 0)
     for (int a = 0; a < MCL; ++a) sm.sc->its[a] = 0;
   __syncthreads();
@@ -202,10 +223,10 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
         acc[5 * L + a] += bv * bv;
       }
     }
-    store_part<6 * L>(acc, qbits(active, L, 6), sm.box, sp.partials, slot);
-    if (!gsync(sp)) return false;
+    store_part<6 * L>(acc, qbits(active, L, 6), sm.box, sp.partials, slot, tm);
+    if (!gsync(ip, tm)) return false;
     double t[6 * L];
-    sum_part<6 * L>(sp.partials, slot, sm.res, t);
+    sum_part<6 * L>(sp.partials, slot, sm.res, t, tm);
     slot ^= 1;
     double shift[L];
     unsigned inner = 0;
@@ -216,11 +237,17 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
       if (sweep == 0) bb[a] = t[5 * L + a];
       const double c = t[2 * L + a] > 0.0 ? t[L + a] / t[2 * L + a] : 0.0;
       shift[a] = c;
-      const double rr = t[a] - 2.0 * c * t[3 * L + a] + c * c * t[4 * L + a];
-      if (rr > rtol2 * bb[a]) inner |= 1u << a;
+      double rr = t[a] - 2.0 * c * t[3 * L + a] + c * c * t[4 * L + a];
+      if (rr < 0.0) rr = 0.0;
+      rr_last[a] = rr;
+      if (rr > rtol2 * bb[a]) {
+        const bool flat = sweep > 0 && (iok & (1u << a)) && rr > 0.25 * rr_prev[a];
+        if (!(flat && rr <= 1e6 * rtol2 * bb[a])) inner |= 1u << a;
+      }
+      rr_prev[a] = rr;
     }
     if (inner && sweep >= ip.ir_max) {
-      if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_NOCONV);
+      if (tm.rank == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_NOCONV);
       return false;
     }
     // ---- 2. apply the shift; start the inner solve on the corrected residual
@@ -251,21 +278,22 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
     active = inner;
     if (!active) break;
     ++sweeps;
-    store_part<2 * L>(acc2, qbits(inner, L, 2), sm.box, sp.partials, slot);
-    if (!gsync(sp)) return false;
-    sum_totals<2 * L>(sp.partials, slot, sm.res);
+    store_part<2 * L>(acc2, qbits(inner, L, 2), sm.box, sp.partials, slot, tm);
+    if (!gsync(ip, tm)) return false;
+    sum_totals<2 * L>(sp.partials, slot, sm.res, tm);
     slot ^= 1;
     InnerScal& S = *sm.sc;
     if (tid == 0) {
       unsigned a_act = 0;
       for (int a = 0; a < L; ++a) {
-        S.rr0[a] = S.rr[a] = S.rck[a] = sm.res[a];
+        S.rr0[a] = S.rr[a] = S.rmin[a] = S.rck[a] = sm.res[a];
         S.rz[a] = sm.res[L + a];
         S.beta[a] = 0.f;
         S.alpha[a] = 0.f;
         if ((active & (1u << a)) && sm.res[a] > 0.0) a_act |= 1u << a;
       }
       S.act = a_act;
+      S.iok = 0;
       S.brk = 0;
     }
     __syncthreads();
@@ -275,10 +303,18 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
     int it = 0;
     const int tiles = sp.tiles_x * sp.tiles_y;
     const int lx = tid % TX, ly = tid / TX;
-    // inner iterations per sweep: restarting the FP32 CG from the refined
-    // FP64 residual beats a long stalled FP32 run
-    int inner_cap = 4 * (nx > ny ? nx : ny);
-    if (inner_cap < 512) inner_cap = 512;
+    // The inner solve ends at inner_rtol, when FP32 CG stops making progress
+    // (the window test below), or at a cap of 16 max(nx, ny) iterations
+    // within [2048, 16384] (and max_iter). The cap has two sides: on a
+    // fracture continuum (k 1e4 in thin connected networks, 1e-2 around
+    // them) Jacobi-PCG needs about 10 n iterations for the 1e-3 reduction,
+    // and cutting that short multiplies the total work; but a very long
+    // FP32 run drifts (its recursive residual keeps falling while the true
+    // one does not: 100000-iteration sweeps at 4096^2 and contrast 1e5
+    // gained nothing), so the FP64 sweep restarts it.
+    int inner_cap = 16 * (nx > ny ? nx : ny);
+    if (inner_cap < 2048) inner_cap = 2048;
+    if (inner_cap > 16384) inner_cap = 16384;
     if (inner_cap > sp.max_iter) inner_cap = sp.max_iter;
     while (act) {
       if (it >= inner_cap) break;  // the outer loop measures what was reached
@@ -305,8 +341,8 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
         tma_load_2d(base + ABOX, &maps.P[cur][a0], bx0, by0, bar);
         tma_load_2d(base + 2 * ABOX, &maps.invd[a0], bx0, by0, bar);
       };
-      const int G = gridDim.x;
-      int tk = blockIdx.x, k = 0;
+      const int G = tm.size;
+      int tk = tm.rank, k = 0;
       unsigned pend = 0;
 #pragma unroll
       for (int j = 0; j < NST - 1; ++j) {
@@ -349,7 +385,7 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
           }
         }
         if (!mbar_wait(sm.bar + s, (phb >> s) & 1u, sp.spin_limit)) {
-          if (tid == 0) grid_raise_abort(irbar(sp), (int)MC_E_TIMEOUT);
+          if (tid == 0) grid_raise_abort(irbar(ip, tm), (int)MC_E_TIMEOUT);
           tma_ok = false;
           break;
         }
@@ -385,9 +421,9 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
           if (pend & (1u << st)) mbar_wait(sm.bar + st, (phb >> st) & 1u, 1LL << 24);
         return false;
       }
-      store_part_f<L>(pq, act, sm.box, sp.partials, slot);
-      if (!gsync(sp)) return false;
-      sum_totals<L>(sp.partials, slot, sm.res);
+      store_part_f<L>(pq, act, sm.box, sp.partials, slot, tm);
+      if (!gsync(ip, tm)) return false;
+      sum_totals<L>(sp.partials, slot, sm.res, tm);
       slot ^= 1;
       if (tid == 0) {
         int b = 0;
@@ -435,9 +471,9 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
         acc3[a] += srr;
         acc3[L + a] += srz;
       }
-      store_part_f<2 * L>(acc3, qbits(act, L, 2), sm.box, sp.partials, slot);
-      if (!gsync(sp)) return false;
-      sum_totals<2 * L>(sp.partials, slot, sm.res);
+      store_part_f<2 * L>(acc3, qbits(act, L, 2), sm.box, sp.partials, slot, tm);
+      if (!gsync(ip, tm)) return false;
+      sum_totals<2 * L>(sp.partials, slot, sm.res, tm);
       slot ^= 1;
       ++it;
       if (tid == 0) {
@@ -450,13 +486,17 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
           S.beta[a] = (float)(rzn / S.rz[a]);
           S.rz[a] = rzn;
           S.its[a] += 1;
+          if (!(rr > in2 * S.rr0[a])) S.iok |= 1u << a;
           if (!(rr > in2 * S.rr0[a]) || !isfinite(rr)) a_act &= ~(1u << a);
-          // FP32 stagnation: no decrease at all over 512 iterations (CG
-          // residual norms are not monotone, so only a flat stretch counts);
-          // the outer FP64 sweep takes over from what was reached
-          if ((it & 511) == 0) {
-            if (!(rr < S.rck[a])) a_act &= ~(1u << a);
-            S.rck[a] = rr;
+          // FP32 progress test: the smallest residual seen must halve in
+          // every window of 2048 iterations (CG residual norms are not
+          // monotone, so the running minimum is compared); a slower FP32 run
+          // has hit its rounding limits and the outer FP64 sweep restarts
+          // from what was reached
+          if (rr < S.rmin[a]) S.rmin[a] = rr;
+          if ((it & 2047) == 0) {
+            if (!(S.rmin[a] < 0.25 * S.rck[a])) a_act &= ~(1u << a);
+            S.rck[a] = S.rmin[a];
           }
         }
         S.act = a_act;
@@ -465,35 +505,47 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
       act = S.act;
       cur ^= 1;
     }
+    iok = S.iok;
     // ---- 4. x += d (FP64) -------------------------------------------------------
 #pragma unroll
     for (int a = 0; a < L; ++a) {
       if (!(active & (1u << a))) continue;
       for (long long i = gtid; i < Np; i += gs) sp.p[a][i] = __ldcg(sp.p[a] + i) + (double)__ldcg(ip.d32[a] + i);
     }
-    if (!gsync(sp)) return false;
+    if (!gsync(ip, tm)) return false;
   }
-  if (blockIdx.x == 0 && tid == 0) {
+  if (tm.rank == 0 && tid == 0) {
 #pragma unroll
     for (int a = 0; a < L; ++a) {
       if (!(mask & (1u << a))) continue;
       sp.iters[a] += sm.sc->its[a];
       if (sm.sc->its[a] > sp.max_iters[a]) sp.max_iters[a] = sm.sc->its[a];
+      sp.relres[a] = bb[a] > 0.0 ? sqrt(rr_last[a] / bb[a]) : sqrt(rr_last[a]);
     }
     atomicAdd(ip.ir_sweeps, sweeps);
   }
-  return gsync(sp);
+  return gsync(ip, tm);
 }
 
+// One time step of one instance: the D-scheme solves every continuum at once,
+// the L- and U-schemes one continuum after the other (index / reverse order).
 template <int L, typename TT>
-__global__ void __launch_bounds__(NT, 1)
-    ir_step_kernel(const __grid_constant__ IrParams ip, const __grid_constant__ TmaMaps maps) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ bool ir_instance_step(const IrParams& ip, const TmaMaps& maps, Sm& sm, uint32_t& phb,
+                                 int& slot) {
+  const int scheme = ip.sp.scheme;
+  if (scheme == MC_SCHEME_D) return ir_solve<L, TT>(ip, maps, (1u << L) - 1u, sm, phb, slot);
+  for (int k = 0; k < L; ++k) {
+    const int a = scheme == MC_SCHEME_U ? L - 1 - k : k;
+    if (!ir_solve<L, TT>(ip, maps, 1u << a, sm, phb, slot)) return false;
+  }
+  return true;
+}
+
+// Shared-memory carve-up common to both kernels.
+__device__ __forceinline__ void carve(Sm& sm, unsigned char* smem_raw, InnerScal* sc) {
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
-  __shared__ InnerScal s_scal;
-  Sm sm;
-  sm.sc = &s_scal;
+  sm.sc = sc;
   sm.box = reinterpret_cast<float*>(base);
   sm.pn = sm.box + NST * 3 * ABOX;
   sm.red = reinterpret_cast<double*>(sm.pn + ((PN + 1) / 2) * 2);
@@ -504,6 +556,17 @@ __global__ void __launch_bounds__(NT, 1)
     fence_mbar_init();
   }
   __syncthreads();
+}
+
+template <int L, typename TT>
+__global__ void __launch_bounds__(NT, 1)
+    ir_step_kernel(const __grid_constant__ IrParams ip, const __grid_constant__ TmaMaps maps) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ InnerScal s_scal;
+  Sm sm;
+  sm.team.rank = blockIdx.x;
+  sm.team.size = gridDim.x;
+  carve(sm, smem_raw, &s_scal);
   uint32_t phb = 0u;
   int slot = 0;
   const StepParams& sp = ip.sp;
@@ -514,18 +577,124 @@ __global__ void __launch_bounds__(NT, 1)
   for (int step = 0; step < sp.nsteps && ok; ++step) {
     for (int a = 0; a < L; ++a)
       for (long long i = gtid; i < sp.Np; i += gs) sp.pprev[a][i] = __ldcg(sp.p[a] + i);
-    if (!gsync(sp)) { ok = false; break; }
-    if (sp.scheme == MC_SCHEME_D) {
-      ok = ir_solve<L, TT>(ip, maps, (1u << L) - 1u, sm, phb, slot);
-    } else {
-      for (int k = 0; k < L && ok; ++k) {
-        const int a = sp.scheme == MC_SCHEME_U ? L - 1 - k : k;
-        ok = ir_solve<L, TT>(ip, maps, 1u << a, sm, phb, slot);
-      }
-    }
+    if (!gsync(ip, sm.team)) { ok = false; break; }
+    ok = ir_instance_step<L, TT>(ip, maps, sm, phb, slot);
     if (ok) ++done;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *sp.steps_done = done;
+}
+
+// Batched form: one launch advances every instance of a batch by one step.
+// CTA b belongs to team b / team; each team takes the next instance from the
+// shared counter (instances are listed largest first, so the long solves
+// start early and the short ones fill the tail), copies its parameters to
+// shared memory, points the reductions and barriers at the team's own words,
+// and runs the step with team-scoped barriers. Continua converge
+// independently inside each solve (per-continuum active masks; converged
+// continua drop out of the tile list). An instance whose solve fails
+// (refinement limit) is put back to the start of the step and skipped until
+// the host resets it; a barrier timeout anywhere raises the abort word and
+// every team leaves.
+template <typename TT>
+__global__ void __launch_bounds__(NT, 1) ir_batch_kernel(const __grid_constant__ BatchParams bp) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ InnerScal s_scal;
+  __shared__ __align__(16) IrParams s_ip;
+  __shared__ int s_idx, s_flag;
+  static_assert(sizeof(IrParams) % 8 == 0, "IrParams copy in 8-byte words");
+  const int t = blockIdx.x / bp.team;
+  if (t >= bp.teams) return;
+  Sm sm;
+  sm.team.rank = blockIdx.x - t * bp.team;
+  sm.team.size = bp.team;
+  carve(sm, smem_raw, &s_scal);
+  const int tid = threadIdx.x;
+  const bool lead = sm.team.rank == 0 && tid == 0;
+  unsigned* tc = bp.ctrl + 32 * (t + 1);
+  GridBar tb;
+  tb.count = reinterpret_cast<unsigned long long*>(tc);
+  tb.abort_word = bp.abort_word;
+  tb.status = reinterpret_cast<int*>(bp.ctrl + 1);
+  tb.spin_limit = bp.spin_limit;
+  tb.nparts = (unsigned)bp.team;
+  if (tid == 0) s_flag = ld_acquire_u32(bp.abort_word) != 0u;
+  __syncthreads();
+  if (s_flag) return;
+  uint32_t phb = 0u;
+  int slot = 0;
+  const long long gtid = (long long)sm.team.rank * NT + tid;
+  const long long gs = (long long)bp.team * NT;
+  for (;;) {
+    // the team lead draws the next instance; the barrier publishes it
+    if (lead) {
+      const unsigned v = atomicAdd(bp.ctrl, 1u);
+      *reinterpret_cast<volatile unsigned*>(tc + 4) = v;
+    }
+    if (!grid_barrier(tb)) break;
+    if (tid == 0) s_idx = (int)ld_acquire_u32(tc + 4);
+    __syncthreads();
+    const int idx = s_idx;
+    if (idx >= bp.n) break;
+    const int inst = __ldg(bp.order + idx);
+    {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(bp.inst + inst);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s_ip);
+      for (int w = tid; w < (int)(sizeof(IrParams) / 8); w += NT) dst[w] = __ldg(src + w);
+    }
+    __syncthreads();
+    BatchInst* rec = bp.st + inst;
+    if (tid == 0) {
+      StepParams& sp = s_ip.sp;
+      sp.scheme = bp.scheme;
+      sp.rtol = bp.rtol;
+      sp.max_iter = bp.max_iter;
+      sp.spin_limit = bp.spin_limit;
+      sp.partials = bp.partials + (size_t)t * 2 * KM * bp.team;
+      sp.bar_count = tc;
+      sp.status = &rec->status;
+      sp.iters = rec->iters;
+      sp.max_iters = rec->max_iters;
+      sp.relres = rec->relres;
+      s_ip.inner_rtol = bp.inner_rtol;
+      s_ip.ir_max = bp.ir_max;
+      s_ip.ir_sweeps = &rec->ir_sweeps;
+      s_ip.abort_word = bp.abort_word;
+      s_flag = __ldcg(&rec->status) != 0;
+    }
+    __syncthreads();
+    if (s_flag) {  // failed earlier in this call: leave it as it is
+      if (!grid_barrier(tb)) break;
+      continue;
+    }
+    const StepParams& sp = s_ip.sp;
+    const int L = sp.L;
+    for (int a = 0; a < L; ++a)
+      for (long long i = gtid; i < sp.Np; i += gs) sp.pprev[a][i] = __ldcg(sp.p[a] + i);
+    if (!gsync(s_ip, sm.team)) break;
+    if (lead) rec->busy = 1;
+    const TmaMaps& maps = bp.maps[inst];
+    bool ok;
+    switch (L) {
+      case 1: ok = ir_instance_step<1, TT>(s_ip, maps, sm, phb, slot); break;
+      case 2: ok = ir_instance_step<2, TT>(s_ip, maps, sm, phb, slot); break;
+      case 3: ok = ir_instance_step<3, TT>(s_ip, maps, sm, phb, slot); break;
+      default: ok = ir_instance_step<4, TT>(s_ip, maps, sm, phb, slot); break;
+    }
+    if (ok) {
+      if (lead) {
+        rec->steps_done += 1;
+        rec->busy = 0;
+      }
+      continue;
+    }
+    if (tid == 0) s_flag = ld_acquire_u32(bp.abort_word) != 0u;
+    __syncthreads();
+    if (s_flag) break;  // timeout: the host restores instances left busy
+    for (int a = 0; a < L; ++a)
+      for (long long i = gtid; i < sp.Np; i += gs) sp.p[a][i] = __ldcg(sp.pprev[a] + i);
+    if (!gsync(s_ip, sm.team)) break;
+    if (lead) rec->busy = 0;
+  }
 }
 
 template <int L, typename TT>
@@ -630,30 +799,66 @@ cudaError_t mc_ir_prepare(mc_ctx* ctx, int bf16) {
   return cudaSuccess;
 }
 
+void mc_ir_fill(const mc_ctx* ctx, const StepParams& sp_in, IrParams* ip) {
+  memset(ip, 0, sizeof(*ip));
+  ip->sp = sp_in;
+  ip->sp.tiles_x = (sp_in.nx + TX - 1) / TX;
+  ip->sp.tiles_y = (sp_in.ny + TY - 1) / TY;
+  for (int a = 0; a < ctx->L; ++a) {
+    ip->r32[a] = ctx->r32[a];
+    ip->P32[0][a] = ctx->P32[0][a];
+    ip->P32[1][a] = ctx->P32[1][a];
+    ip->q32[a] = ctx->q32[a];
+    ip->d32[a] = ctx->d32[a];
+    ip->invd32[a] = ctx->invd32[a];
+    ip->TElo[a] = ctx->TElo32[a];
+    ip->TNlo[a] = ctx->TNlo32[a];
+    ip->dc32[a] = ctx->dc32[a];
+    ip->dcf[a] = (float)sp_in.diagc_const[a];
+  }
+  ip->inner_rtol = ctx->opts.inner_rtol;
+  ip->ir_max = ctx->opts.ir_max;
+  ip->ir_sweeps = ctx->dsweeps;
+  ip->abort_word = sp_in.bar_gen + 32;
+}
+
 cudaError_t mc_launch_ir(mc_ctx* ctx, const StepParams& sp_in, int bf16, int blocks) {
   IrParams ip;
-  memset(&ip, 0, sizeof(ip));
-  ip.sp = sp_in;
-  ip.sp.tiles_x = (sp_in.nx + TX - 1) / TX;
-  ip.sp.tiles_y = (sp_in.ny + TY - 1) / TY;
-  for (int a = 0; a < ctx->L; ++a) {
-    ip.r32[a] = ctx->r32[a];
-    ip.P32[0][a] = ctx->P32[0][a];
-    ip.P32[1][a] = ctx->P32[1][a];
-    ip.q32[a] = ctx->q32[a];
-    ip.d32[a] = ctx->d32[a];
-    ip.invd32[a] = ctx->invd32[a];
-    ip.TElo[a] = ctx->TElo32[a];
-    ip.TNlo[a] = ctx->TNlo32[a];
-    ip.dc32[a] = ctx->dc32[a];
-    ip.dcf[a] = (float)sp_in.diagc_const[a];
-  }
-  ip.inner_rtol = ctx->opts.inner_rtol;
-  ip.ir_max = ctx->opts.ir_max;
-  ip.ir_sweeps = ctx->dsweeps;
+  mc_ir_fill(ctx, sp_in, &ip);
   IKInfo k = ipick(ctx->L, bf16 != 0);
   cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
   if (e != cudaSuccess) return e;
   void* args[] = {&ip, &ctx->maps32};
   return cudaLaunchCooperativeKernel(k.fn, dim3(blocks), dim3(NT), args, k.smem, ctx->stream);
+}
+
+static void* batch_fn(bool bf16) {
+  return bf16 ? (void*)ir_batch_kernel<__nv_bfloat16> : (void*)ir_batch_kernel<float>;
+}
+
+int mc_ir_batch_max_blocks(bool bf16, int num_sms) {
+  void* fn = batch_fn(bf16);
+  const size_t smem = ir_smem<1, float>();
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, NT, smem) != cudaSuccess) return 0;
+  return per * num_sms;
+}
+
+cudaError_t mc_launch_ir_batch(const BatchParams& bp, int bf16, int blocks, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = ir_smem<1, float>();
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  BatchParams copy = bp;
+  void* args[] = {&copy};
+  return cudaLaunchKernelExC(&cfg, batch_fn(bf16 != 0), args);
 }

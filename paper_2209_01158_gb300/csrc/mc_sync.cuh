@@ -19,6 +19,7 @@ struct GridBar {
   unsigned* abort_word;       // zeroed before the launch
   int* status;
   long long spin_limit;
+  unsigned nparts;            // CTAs taking part (0: the whole grid)
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -53,7 +54,7 @@ __device__ __forceinline__ bool grid_barrier(const GridBar& g) {
   if (threadIdx.x == 0) {
     int ok = 1;
     __threadfence();
-    const unsigned long long G = gridDim.x;
+    const unsigned long long G = g.nparts ? g.nparts : gridDim.x;
     const unsigned long long old = atom_add_release_u64(g.count, 1ull);
     const unsigned long long target = (old / G + 1ull) * G;
     long long n = 0;
@@ -112,7 +113,12 @@ __device__ __forceinline__ void cta_sum(double (&v)[NQ], double* s_red, double* 
 // skipped and stored as 0. `stage` needs 8 * NTH elements.
 template <int NQ, int NTH, int KM, typename T>
 __device__ __forceinline__ void cta_reduce_store(const T (&v)[NQ], unsigned qmask, T* stage,
-                                                 double* partials, int slot) {
+                                                 double* partials, int slot, int nb = -1,
+                                                 int b = -1) {
+  if (nb < 0) {
+    nb = gridDim.x;
+    b = blockIdx.x;
+  }
   static_assert(NTH % 32 == 0 && NTH >= 256, "block size");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
@@ -131,7 +137,7 @@ __device__ __forceinline__ void cta_reduce_store(const T (&v)[NQ], unsigned qmas
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       }
-      if (lane == 0) partials[((size_t)slot * KM + k) * gridDim.x + blockIdx.x] = (double)s;
+      if (lane == 0) partials[((size_t)slot * KM + k) * nb + b] = (double)s;
     }
     __syncthreads();
   }

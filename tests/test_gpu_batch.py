@@ -1,0 +1,192 @@
+"""GPU parity of the batched precision form: independent instances of uneven
+sizes and numbers of continua (the fracture recipe of the batched workload),
+stepped together, one persistent launch per step, the loop replayed from a
+CUDA graph.
+
+Bar: every instance within relative L2 1e-8 of its own FP64 oracle run (the
+mixed-precision target). The fracture continuum (k 1e4 on thin networks,
+1e-2 around them) is ill-conditioned enough that a relative residual of
+1e-10 leaves errors up to ~3e-8, so the outer FP64 residual is driven to
+rtol 1e-12.
+"""
+
+import json
+
+import numpy as np
+import pytest
+
+import mc_inputs as mi
+from oracle import metrics
+from oracle.schemes import from_workload
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-8
+
+# (seed, n, L): ragged sizes (not multiples of the 64 x 16 tile), L = 2 and 3
+SHAPES = [(4101, 40, 2), (4102, 72, 3), (4103, 96, 2), (4104, 33, 3), (4105, 130, 2),
+          (4106, 64, 3)]
+
+
+@pytest.fixture(scope="module")
+def mc():
+    import paper_2209_01158_gb300 as m
+    m._lib()
+    return m
+
+
+def opts(mc, precision=1, rtol=1e-12, **kw):
+    o = mc.mc_default_opts()
+    o.precision = precision
+    o.rtol = rtol
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def instances(shapes=SHAPES):
+    return [mi.fracture_instance(s, n=n, L=L) for (s, n, L) in shapes]
+
+
+def oracle_runs(ws, nsteps, scheme):
+    return [from_workload(w).run(w.p0, w.F, nsteps, scheme) for w in ws]
+
+
+@pytest.fixture(scope="module")
+def ws():
+    return instances()
+
+
+@pytest.fixture(scope="module")
+def ref_d4(ws):
+    return oracle_runs(ws, 4, "D")
+
+
+@pytest.mark.parametrize("team", [None, 1, 3, 16])
+def test_batch_d_scheme_matches_oracle(mc, ws, ref_d4, team):
+    o = opts(mc)
+    ctxs = [mc.Context.from_workload(w, opts=o) for w in ws]
+    b = mc.Batch(ctxs, o, team=team)
+    st = b.step("D", 4)
+    assert st["steps_done"] == 4 and st["status"] == 0
+    info = b.info()
+    assert info["graph"] == 1
+    if team is not None:
+        assert info["team"] == team
+    for i, (c, ref) in enumerate(zip(ctxs, ref_d4)):
+        err = metrics.rel_l2(ref, c.get_state())
+        assert err <= MIXED_TOL, (i, err, b.instance_stats(i))
+        s = b.instance_stats(i)
+        assert s["steps_done"] == 4 and s["ir_sweeps"] > 0
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
+@pytest.mark.parametrize("scheme", ["L", "U"])
+def test_batch_sequential_schemes(mc, scheme):
+    ws = instances(SHAPES[:4])
+    ref = oracle_runs(ws, 3, scheme)
+    o = opts(mc)
+    ctxs = [mc.Context.from_workload(w, opts=o) for w in ws]
+    b = mc.Batch(ctxs, o, team=2)
+    b.step(scheme, 3)
+    for i, c in enumerate(ctxs):
+        assert metrics.rel_l2(ref[i], c.get_state()) <= MIXED_TOL, i
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_batch_bf16_transmissibilities(mc):
+    ws = instances(SHAPES[:3])
+    ref = oracle_runs(ws, 3, "D")
+    o = opts(mc, precision=2)
+    ctxs = [mc.Context.from_workload(w, opts=o) for w in ws]
+    b = mc.Batch(ctxs, o)
+    b.step("D", 3)
+    for i, c in enumerate(ctxs):
+        assert metrics.rel_l2(ref[i], c.get_state()) <= MIXED_TOL, i
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_batch_graph_replay_and_host_updates(mc, ws, ref_d4):
+    """Two calls of 2 steps replay one captured graph; a state set between
+    calls through a member context is seen by the next batched step."""
+    o = opts(mc)
+    ctxs = [mc.Context.from_workload(w, opts=o) for w in ws]
+    b = mc.Batch(ctxs, o, team=4)
+    b.step("D", 2)
+    b.step("D", 2)
+    for i, c in enumerate(ctxs):
+        assert metrics.rel_l2(ref_d4[i], c.get_state()) <= MIXED_TOL, i
+    # restart instance 0 from p0 and step it (with the others) twice more
+    ctxs[0].set_state(ws[0].p0)
+    b.step("D", 2)
+    ref0 = from_workload(ws[0]).run(ws[0].p0, ws[0].F, 2, "D")
+    assert metrics.rel_l2(ref0, ctxs[0].get_state()) <= MIXED_TOL
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_batch_failed_instance_is_isolated(mc):
+    """ir_max = 0 allows no refinement sweep: instances with a source fail
+    (MC_E_NOCONV) and are put back to the start of the step; an instance with
+    no source and zero state needs no sweep and completes every step."""
+    ws = instances(SHAPES[:3])
+    quiet = mi.fracture_instance(4199, n=48, L=2)
+    quiet.F = [np.zeros_like(f) for f in quiet.F]
+    ws.append(quiet)
+    o = opts(mc, ir_max=0)
+    ctxs = [mc.Context.from_workload(w, opts=o) for w in ws]
+    b = mc.Batch(ctxs, o, team=2)
+    st = b.step("D", 3, check=False)
+    assert st["return"] == mc.N.MC_E_NOCONV
+    for i in range(3):
+        s = b.instance_stats(i)
+        assert s["status"] == mc.N.MC_E_NOCONV and s["steps_done"] == 0
+        for a, x in enumerate(ctxs[i].get_state()):
+            assert np.array_equal(x, np.ravel(ws[i].p0[a]))
+    s = b.instance_stats(3)
+    assert s["status"] == 0 and s["steps_done"] == 3
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_autotune_keeps_state_and_caches(mc, ws, tmp_path):
+    cache = str(tmp_path / "tune.json")
+    o = opts(mc)
+    ctxs = [mc.Context.from_workload(w, opts=o) for w in ws[:4]]
+    b = mc.Batch(ctxs, o)
+    b.step("D", 1)
+    before = [c.get_state() for c in ctxs]
+    best, ms = b.autotune("D", candidates=[1, 2, 4, 8], cache_path=cache)
+    assert best in (1, 2, 4, 8)
+    assert all(t > 0 for t in ms)
+    after = [c.get_state() for c in ctxs]
+    for x, y in zip(before, after):
+        for u, v in zip(x, y):
+            assert np.array_equal(u, v)
+    data = json.load(open(cache))
+    assert len(data) == 1 and list(data.values())[0]["team"] == best
+    assert b.info()["team"] == best and b.info()["from_cache"] == 0
+    b.close()
+    # a batch of the same shapes (other order) hits the cache
+    b2 = mc.Batch(ctxs[::-1], o)
+    best2, _ = b2.autotune("D", candidates=[1, 2, 4, 8], cache_path=cache)
+    assert best2 == best and b2.info()["from_cache"] == 1
+    b2.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_batch_rejects_fp64(mc):
+    w = mi.fracture_instance(4101, n=32, L=2)
+    ctx = mc.Context.from_workload(w)
+    with pytest.raises(mc.MCError):
+        mc.Batch([ctx], opts(mc, precision=0))
+    ctx.close()
