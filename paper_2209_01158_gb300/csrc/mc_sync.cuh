@@ -2,7 +2,8 @@
 // (cooperative) kernels of libmc.so.
 //
 // The barrier is a monotonic 64-bit arrival counter: barrier number b is
-// passed when the counter reaches (b + 1) * gridDim.x, so one release atomic
+// passed when the counter reaches (b + 1) * G, G the CTAs taking part (the
+// whole grid, or one team of the batched kernel), so one release atomic
 // per CTA and acquire polls suffice (no reset, no generation word). Every
 // wait is bounded by `spin_limit` polls; a CTA that gives up raises the abort
 // word and the status MC_E_TIMEOUT, and CTAs that see the abort word while
@@ -15,11 +16,11 @@
 #include "../../include/mc.h"
 
 struct GridBar {
-  unsigned long long* count;  // zeroed before the launch
-  unsigned* abort_word;       // zeroed before the launch
-  int* status;
-  long long spin_limit;
-  unsigned nparts;            // CTAs taking part (0: the whole grid)
+  unsigned long long* count = nullptr;  // zeroed before the launch
+  unsigned* abort_word = nullptr;       // zeroed before the launch
+  int* status = nullptr;
+  long long spin_limit = 0;
+  unsigned nparts = 0;                  // CTAs taking part (0: the whole grid)
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
