@@ -42,6 +42,7 @@ BYTES_PER_CELL_IT = 88.0     # 11 FP64 values per continuum-cell PCG iteration
 BYTES_PER_CELL_IT_32 = 44.0  # the same 11 values in FP32
 RTOL_D = 1e-10
 RTOL_COUPLED = 1e-11
+RTOL_BATCH = 1e-12           # fracture continua: rtol 1e-10 leaves errors up to ~3e-8
 SMI_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -57,6 +58,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="only the headline D-scheme line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--crop", type=int, default=384, help="oracle sample size (cells per side)")
+    ap.add_argument("--batch", type=int, default=64,
+                    help="instances of the batched fracture workload (seeds 4000..; 0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=1, help="timed batched steps")
     ap.add_argument("--profile-step", type=int, default=-1, metavar="PRECISION",
                     help="profiling case: one warm-up and one D-scheme step of the workload at "
                          "--n with this precision (0 FP64, 1 FP32 IR, 2 BF16 IR), nothing else")
@@ -206,6 +210,54 @@ def run_reference(args, ws, rank):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def batched_extra(args, mc, mi, torch, stream, ws):
+    """The batched fracture workload (256 instances of 128^2..1024^2, L = 2
+    or 3, in the full recipe; the first --batch of them here): one warm-up
+    step (graph capture, and instances whose FP32 refinement fails are handed
+    to the FP64 path), then --batch-steps timed steps, wall clock around
+    mc_batch_step (which synchronises). Accuracy: the three smallest
+    instances against the oracle."""
+    from oracle import metrics
+    from oracle.schemes import from_workload
+    wb = mi.batched_instances(args.batch)
+    ob = mc.mc_default_opts()
+    ob.precision = 1
+    ob.rtol = RTOL_BATCH
+    ob.ir_max = 12
+    ctxs = [mc.Context.from_workload(x, opts=ob, stream=stream) for x in wb]
+    bt = mc.Batch(ctxs, ob)
+    bt.step("D", 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = bt.step("D", args.batch_steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    info = bt.info()
+    small = sorted(range(len(wb)), key=lambda i: wb[i].nx * wb[i].ny * wb[i].L)[:3]
+    errs = []
+    for i in small:
+        ref = from_workload(wb[i]).run(wb[i].p0, wb[i].F, 1 + args.batch_steps, "D")
+        errs.append(metrics.rel_l2(ref, ctxs[i].get_state()))
+    sizes = {}
+    for x in wb:
+        sizes["%dx%d_L%d" % (x.nx, x.ny, x.L)] = sizes.get("%dx%d_L%d" % (x.nx, x.ny, x.L), 0) + 1
+    bt.close()
+    for c in ctxs:
+        c.close()
+    return {"workload": "batched fracture instances, seeds 4000..%d (sizes %s), D-scheme, FP32 "
+                        "inner PCG + FP64 refinement, rtol %g, ir_max 12" % (
+                            4000 + args.batch - 1, sizes, RTOL_BATCH),
+            "value": ws * info["continuum_cells"] * args.batch_steps / dt,
+            "unit": "continuum-cell updates/s", "steps": args.batch_steps, "s_per_step": dt / args.batch_steps,
+            "timing": "host wall clock around mc_batch_step (one graph replay + FP64 path for "
+                      "handed-over instances), after one warm-up step",
+            "team": info["team"], "teams": info["teams"],
+            "fp64_instances": info["fp64_instances"],
+            "inner_iterations_per_step": float(sum(st["iters"])) / args.batch_steps,
+            "ir_sweeps_per_step": st["ir_sweeps"] / args.batch_steps,
+            "max_rel_l2_vs_oracle_3_smallest": max(errs)}
 
 
 def main():
@@ -363,6 +415,9 @@ def main():
                           "build_s": t_build, "basis_pcg_iterations": info["basis_iters"],
                           "coarse_steps_per_s": ncs / t_coarse,
                           "coarse_D_e_H_after_5_steps_vs_fine_coupled": e_h}
+
+    if not args.no_extras and args.batch > 0:
+        extras["batched"] = batched_extra(args, mc, mi, torch, stream, ws)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -82,7 +82,8 @@ typedef struct {
   double rtol;         /* stop when ||b - A x||_2 <= rtol ||b||_2 (FP64). IR
                           forms also stop at the floor of refinement (an inner
                           solve met inner_rtol but the sweep did not halve
-                          ||r||) when that floor is within 1e3 rtol ||b||;
+                          ||r||) when that floor is within 1e3 rtol ||b|| or
+                          the last correction was below 100 rtol ||x||;
                           rel_residual reports what was met */
   double inner_rtol;   /* inner PCG relative residual target of each IR sweep
                           (default 1e-3) */
@@ -269,14 +270,20 @@ mc_status mc_batch_set_team(mc_batch* b, int32_t team);
 /*
  * mc_batch_step -- nsteps steps of every instance (scheme MC_SCHEME_D, _L
  *   or _U). Per instance and continuum the solve stops on the FP64 residual
- *   test ||b - A x|| <= rtol ||b||. An instance whose solve fails
- *   (MC_E_NOCONV after ir_max sweeps) is put back to the start of that step
- *   and left there for the rest of the call; the others go on. A barrier
- *   timeout stops the whole call (MC_E_TIMEOUT) with every instance at the
- *   end of its last completed step. Returns the status of the first failed
- *   instance (index order); `total` (may be NULL) gets the minimum
- *   steps_done, that status, iteration and sweep counts summed over the
- *   instances (max_iters: the maximum). Synchronises.
+ *   test ||b - A x|| <= rtol ||b|| (or the refinement floor, see mc_opts).
+ *   An instance whose FP32 refinement fails (MC_E_NOCONV after ir_max
+ *   sweeps; on fracture continua at 1024^2 FP32 Jacobi-PCG cannot sustain
+ *   the long Krylov runs the problem needs) is put back to the start of
+ *   that step inside the launch; after the batched launches the host steps
+ *   it through the rest of the call with the FP64 PCG path
+ *   (mc_step_decoupled, same rtol and max_iter), and it stays on that path
+ *   for later calls (count in mc_batch_info). An instance that fails there
+ *   too keeps the start of its failed step. A barrier timeout stops the
+ *   whole call (MC_E_TIMEOUT) with every instance at the end of its last
+ *   completed step. Returns the status of the first failed instance (index
+ *   order); `total` (may be NULL) gets the minimum steps_done, that status,
+ *   iteration and sweep counts summed over the instances (max_iters: the
+ *   maximum). Synchronises.
  */
 mc_status mc_batch_step(mc_batch* b, int32_t scheme, int32_t nsteps, mc_stats* total);
 
@@ -300,10 +307,10 @@ mc_status mc_batch_autotune(mc_batch* b, int32_t scheme, const int32_t* candidat
                             int32_t ncand, const char* cache_path, int32_t* best_team,
                             double* ms);
 
-/* info[0..7] = instances, team size, teams, CTAs per launch, whether the last
+/* info[0..8] = instances, team size, teams, CTAs per launch, whether the last
  * step ran as a graph replay (1/0), whether the team size came from the tuner
  * cache (1/0), continuum cells summed over the instances, device bytes held
- * by the batch itself. */
+ * by the batch itself, instances handed to the FP64 path. */
 mc_status mc_batch_info(const mc_batch* b, int64_t* info);
 
 /* Last error text of b (or of the last failed mc_batch_create when NULL). */

@@ -425,10 +425,11 @@ class Batch:
         return best.value, (list(ms) if ms is not None else None)
 
     def info(self):
-        v = (C.c_int64 * 8)()
+        v = (C.c_int64 * 9)()
         self._check(_lib().mc_batch_info(self._h, v))
         return {"n": v[0], "team": v[1], "teams": v[2], "ctas": v[3], "graph": v[4],
-                "from_cache": v[5], "continuum_cells": v[6], "device_bytes": v[7]}
+                "from_cache": v[5], "continuum_cells": v[6], "device_bytes": v[7],
+                "fp64_instances": v[8]}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -40,6 +40,10 @@ struct mc_batch {
   unsigned* d_abort = nullptr;
   double* d_partials = nullptr;
   std::vector<BatchInst> h_st;
+  std::vector<BatchInst> h_init;       // records at the start of a call
+  // instances whose FP32 refinement failed once: stepped by the FP64 PCG path
+  std::vector<char> fp64;
+  int n_fp64 = 0;
   // the captured time loop
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -185,21 +189,57 @@ cudaError_t restore_busy(mc_batch* b) {
   return cudaSuccess;
 }
 
-// Undo the last step of every instance (p <- p^{n-1}); used by the tuner.
+// Undo the last step of every batched instance (p <- p^{n-1}); used by the
+// tuner (instances on the FP64 path are skipped by the trial launches).
 cudaError_t undo_step(mc_batch* b) {
-  for (mc_ctx* c : b->ctx)
+  for (int i = 0; i < b->n; ++i) {
+    if (b->fp64[i]) continue;
+    mc_ctx* c = b->ctx[i];
     for (int a = 0; a < c->L; ++a) {
       cudaError_t e = cudaMemcpyAsync(c->p[a], c->pprev[a], (size_t)c->Np * sizeof(double),
                                       cudaMemcpyDeviceToDevice, b->stream);
       if (e != cudaSuccess) return e;
     }
+  }
   return cudaSuccess;
 }
 
+// Zeroed records; instances on the FP64 path carry a nonzero status so the
+// batched kernel skips them.
+constexpr int kSkip = -1;
+
 cudaError_t reset_records(mc_batch* b) {
-  cudaError_t e = cudaMemsetAsync(b->d_st, 0, sizeof(BatchInst) * b->n, b->stream);
+  b->h_init.assign(b->n, BatchInst{});
+  for (int i = 0; i < b->n; ++i)
+    if (b->fp64[i]) b->h_init[i].status = kSkip;
+  cudaError_t e = cudaMemcpyAsync(b->d_st, b->h_init.data(), sizeof(BatchInst) * b->n,
+                                  cudaMemcpyHostToDevice, b->stream);
   if (e != cudaSuccess) return e;
   return cudaMemsetAsync(b->d_abort, 0, 128, b->stream);
+}
+
+// nsteps steps of instance i by the FP64 PCG path (mc_step_decoupled with
+// the batch's tolerances), added to its record.
+mc_status fp64_steps(mc_batch* b, int i, int scheme, int nsteps) {
+  mc_ctx* c = b->ctx[i];
+  const mc_opts save = c->opts;
+  c->opts.precision = MC_PREC_FP64;
+  c->opts.rtol = b->opts.rtol;
+  c->opts.max_iter = b->opts.max_iter;
+  c->opts.spin_limit = b->opts.spin_limit;
+  c->opts.blocks = 0;
+  mc_stats s;
+  const mc_status st = mc_step_decoupled(c, scheme, nsteps, &s);
+  c->opts = save;
+  BatchInst& r = b->h_st[i];
+  r.steps_done += s.steps_done;
+  r.status = s.status ? s.status : (st == MC_OK ? 0 : (int)st);
+  for (int a = 0; a < MCL; ++a) {
+    r.iters[a] += s.iters[a];
+    r.max_iters[a] = std::max(r.max_iters[a], s.max_iters[a]);
+    r.relres[a] = s.rel_residual[a];
+  }
+  return st;
 }
 
 cudaError_t fetch_records(mc_batch* b, unsigned* abort_word) {
@@ -330,6 +370,7 @@ mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t n, const mc_opts* opts, m
   b->bf16 = opts->precision == MC_PREC_BF16T_IR ? 1 : 0;
   b->ctx.assign(ctxs, ctxs + n);
   b->h_st.assign(n, BatchInst{});
+  b->fp64.assign(n, 0);
   auto fail = [&](mc_status s) {
     g_batch_err = b->err;
     bfree(b);
@@ -444,6 +485,24 @@ mc_status mc_batch_step(mc_batch* b, int32_t scheme, int32_t nsteps, mc_stats* t
   if (abort_word) {
     BK(restore_busy(b));
     BK(cudaStreamSynchronize(b->stream));
+  } else {
+    // FP32 refinement that failed (MC_E_NOCONV: the instance is back at the
+    // start of its failed step) hands the instance to the FP64 PCG path for
+    // the rest of this call and for later calls; instances already there
+    // take all their steps by it.
+    for (int i = 0; i < b->n; ++i) {
+      BatchInst& r = b->h_st[i];
+      if (r.status == kSkip) {
+        r.status = 0;
+      } else if (r.status == MC_E_NOCONV) {
+        b->fp64[i] = 1;
+        ++b->n_fp64;
+        r.status = 0;
+      } else {
+        continue;
+      }
+      fp64_steps(b, i, scheme, nsteps - r.steps_done);
+    }
   }
   mc_stats acc;
   memset(&acc, 0, sizeof(acc));
@@ -580,6 +639,7 @@ mc_status mc_batch_info(const mc_batch* b, int64_t* info) {
   info[5] = b->tuned_from_cache;
   info[6] = (int64_t)cells;
   info[7] = b->bytes;
+  info[8] = b->n_fp64;
   return MC_OK;
 }
 

@@ -14,7 +14,8 @@
 //      its floor: the last inner solve met its own target but the sweep did
 //      not halve ||r|| (the rule LAPACK's refinement uses: stop once the
 //      backward error no longer halves), with ||r|| already within
-//      1e3 rtol ||b||. On fracture continua (k 1e4 on thin networks, 1e-2
+//      1e3 rtol ||b|| or the last correction below 100 rtol ||x||. On
+//      fracture continua (k 1e4 on thin networks, 1e-2
 //      around them) FP32-corrected refinement levels off near 1e-11 ||b||
 //      while the error is ~1e-13: the FP32 corrections carry large
 //      near-null components that the operator maps to small residuals;
@@ -185,10 +186,11 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
   bool ok = true;
   for (int sweep = 0; ok; ++sweep) {
     // ---- 1. FP64 residual and the sums of the constant-mode correction -----
-    // q: [rr, sum r, sum dc, sum r dc, sum dc^2, bb] per continuum
-    double acc[6 * L];
+    // q: [rr, sum r, sum dc, sum r dc, sum dc^2, bb, xx, dd] per continuum
+    // (dd: the last inner correction, still in d32)
+    double acc[8 * L];
 #pragma unroll
-    for (int k = 0; k < 6 * L; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 8 * L; ++k) acc[k] = 0.0;
 #pragma unroll
     for (int a = 0; a < L; ++a) {
       if (!(active & (1u << a))) continue;
@@ -221,12 +223,17 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
         acc[3 * L + a] += rv * dc;
         acc[4 * L + a] += dc * dc;
         acc[5 * L + a] += bv * bv;
+        acc[6 * L + a] += xc * xc;
+        if (sweep > 0) {
+          const double dv = (double)__ldcg(ip.d32[a] + i);
+          acc[7 * L + a] += dv * dv;
+        }
       }
     }
-    store_part<6 * L>(acc, qbits(active, L, 6), sm.box, sp.partials, slot, tm);
+    store_part<8 * L>(acc, qbits(active, L, 8), sm.box, sp.partials, slot, tm);
     if (!gsync(ip, tm)) return false;
-    double t[6 * L];
-    sum_part<6 * L>(sp.partials, slot, sm.res, t, tm);
+    double t[8 * L];
+    sum_part<8 * L>(sp.partials, slot, sm.res, t, tm);
     slot ^= 1;
     double shift[L];
     unsigned inner = 0;
@@ -241,13 +248,27 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
       if (rr < 0.0) rr = 0.0;
       rr_last[a] = rr;
       if (rr > rtol2 * bb[a]) {
+        // refinement floor: the inner solve met its target, ||r|| did not
+        // halve, and either ||r|| is within 1e3 rtol ||b|| or the last
+        // correction moved x by at most 100 rtol ||x||
         const bool flat = sweep > 0 && (iok & (1u << a)) && rr > 0.25 * rr_prev[a];
-        if (!(flat && rr <= 1e6 * rtol2 * bb[a])) inner |= 1u << a;
+        const bool near = rr <= 1e6 * rtol2 * bb[a] || t[7 * L + a] <= 1e4 * rtol2 * t[6 * L + a];
+        if (!(flat && near)) inner |= 1u << a;
       }
       rr_prev[a] = rr;
     }
     if (inner && sweep >= ip.ir_max) {
-      if (tm.rank == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_NOCONV);
+      if (tm.rank == 0 && tid == 0) {
+        atomicCAS(sp.status, 0, (int)MC_E_NOCONV);
+        // what the failed solve reached, for the caller's diagnosis
+        for (int a = 0; a < L; ++a) {
+          if (!(mask & (1u << a))) continue;
+          sp.iters[a] += sm.sc->its[a];
+          if (sm.sc->its[a] > sp.max_iters[a]) sp.max_iters[a] = sm.sc->its[a];
+          sp.relres[a] = bb[a] > 0.0 ? sqrt(rr_last[a] / bb[a]) : sqrt(rr_last[a]);
+        }
+        atomicAdd(ip.ir_sweeps, sweeps);
+      }
       return false;
     }
     // ---- 2. apply the shift; start the inner solve on the corrected residual

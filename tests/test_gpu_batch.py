@@ -132,25 +132,51 @@ def test_batch_graph_replay_and_host_updates(mc, ws, ref_d4):
         c.close()
 
 
-def test_batch_failed_instance_is_isolated(mc):
-    """ir_max = 0 allows no refinement sweep: instances with a source fail
-    (MC_E_NOCONV) and are put back to the start of the step; an instance with
-    no source and zero state needs no sweep and completes every step."""
+def test_batch_failed_refinement_falls_back_to_fp64(mc):
+    """ir_max = 0 allows no refinement sweep: instances with a source fail the
+    FP32 form at their first step, go back to its start, and are stepped by
+    the FP64 PCG path instead (and stay there on the next call); an instance
+    with no source and zero state needs no sweep and stays batched."""
     ws = instances(SHAPES[:3])
     quiet = mi.fracture_instance(4199, n=48, L=2)
     quiet.F = [np.zeros_like(f) for f in quiet.F]
     ws.append(quiet)
+    ref = oracle_runs(ws, 3, "D")
     o = opts(mc, ir_max=0)
+    ctxs = [mc.Context.from_workload(w, opts=o) for w in ws]
+    b = mc.Batch(ctxs, o, team=2)
+    b.step("D", 2)
+    assert b.info()["fp64_instances"] == 3
+    b.step("D", 1)
+    assert b.info()["fp64_instances"] == 3
+    for i, c in enumerate(ctxs):
+        s = b.instance_stats(i)
+        assert s["status"] == 0 and s["steps_done"] == 1, (i, s)
+        assert metrics.rel_l2(ref[i], c.get_state()) <= MIXED_TOL, i
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_batch_failure_keeps_last_state(mc):
+    """With max_iter = 1 and ir_max = 0 neither the FP32 form nor the FP64
+    path can converge: the call reports MC_E_NOCONV and every instance with a
+    source keeps its initial state; the quiet instance completes its steps."""
+    ws = instances(SHAPES[:2])
+    quiet = mi.fracture_instance(4199, n=48, L=2)
+    quiet.F = [np.zeros_like(f) for f in quiet.F]
+    ws.append(quiet)
+    o = opts(mc, ir_max=0, max_iter=1)
     ctxs = [mc.Context.from_workload(w, opts=o) for w in ws]
     b = mc.Batch(ctxs, o, team=2)
     st = b.step("D", 3, check=False)
     assert st["return"] == mc.N.MC_E_NOCONV
-    for i in range(3):
+    for i in range(2):
         s = b.instance_stats(i)
         assert s["status"] == mc.N.MC_E_NOCONV and s["steps_done"] == 0
         for a, x in enumerate(ctxs[i].get_state()):
             assert np.array_equal(x, np.ravel(ws[i].p0[a]))
-    s = b.instance_stats(3)
+    s = b.instance_stats(2)
     assert s["status"] == 0 and s["steps_done"] == 3
     b.close()
     for c in ctxs:
