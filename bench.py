@@ -88,6 +88,17 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def reduce_max(x, ws, device):
+    """Max of x over the ranks (the slowest rank's time decides the
+    whole-job throughput); identity on one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     """(HBM GB/s, FP64 TFLOP/s, source). FP64: 2 FMA lanes per SM per clock
     (ncu's derived peak on GB300) x 152 SMs x 2 FLOP x the max SM clock."""
@@ -217,10 +228,9 @@ def batched_extra(args, mc, mi, torch, stream, ws):
     or 3, in the full recipe; the first --batch of them here): one warm-up
     step (graph capture, and instances whose FP32 refinement fails are handed
     to the FP64 path), then --batch-steps timed steps, wall clock around
-    mc_batch_step (which synchronises). Accuracy: the three smallest
-    instances against the oracle."""
-    from oracle import metrics
-    from oracle.schemes import from_workload
+    mc_batch_step (which synchronises). Parity of the batched form against
+    the oracle is the test suite's job; this line reports the largest final
+    relative residual over the instances."""
     wb = mi.batched_instances(args.batch)
     ob = mc.mc_default_opts()
     ob.precision = 1
@@ -235,11 +245,7 @@ def batched_extra(args, mc, mi, torch, stream, ws):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     info = bt.info()
-    small = sorted(range(len(wb)), key=lambda i: wb[i].nx * wb[i].ny * wb[i].L)[:3]
-    errs = []
-    for i in small:
-        ref = from_workload(wb[i]).run(wb[i].p0, wb[i].F, 1 + args.batch_steps, "D")
-        errs.append(metrics.rel_l2(ref, ctxs[i].get_state()))
+    relres = max(max(bt.instance_stats(i)["rel_residual"]) for i in range(len(wb)))
     sizes = {}
     for x in wb:
         sizes["%dx%d_L%d" % (x.nx, x.ny, x.L)] = sizes.get("%dx%d_L%d" % (x.nx, x.ny, x.L), 0) + 1
@@ -257,7 +263,7 @@ def batched_extra(args, mc, mi, torch, stream, ws):
             "fp64_instances": info["fp64_instances"],
             "inner_iterations_per_step": float(sum(st["iters"])) / args.batch_steps,
             "ir_sweeps_per_step": st["ir_sweeps"] / args.batch_steps,
-            "max_rel_l2_vs_oracle_3_smallest": max(errs)}
+            "max_final_rel_residual": relres}
 
 
 def main():
@@ -288,10 +294,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, ws, "cuda")
 
     w = mi.triple_1024(n=args.n)
     L, Ncell = w.L, w.nx * w.ny
