@@ -40,6 +40,18 @@ sys.path.insert(0, ROOT)
 FLOP_PER_CELL_IT = 26.0      # flux-form stencil 13, p.q 2, x/r updates 4, z 1, r.z 2, r.r 2, p 2
 BYTES_PER_CELL_IT = 88.0     # 11 FP64 values per continuum-cell PCG iteration
 BYTES_PER_CELL_IT_32 = 44.0  # the same 11 values in FP32
+
+
+def inner_bytes_per_cell_it(precision, inner_form):
+    """Algorithmic bytes of one inner FP32 PCG iteration on one continuum-cell.
+
+    Two-reduction form: the 11 values above (TE, TN, invd; x, r, p read and
+    written; q written and read). Single-reduction form: r, s, w, invd, p, d,
+    TE, TN read and r, s, w, p, d written (13 values). BF16 transmissibilities
+    store TE and TN in 2 bytes each.
+    """
+    n_t, n_other = 2, (9 if inner_form == 1 else 11)
+    return n_t * (2 if precision == 2 else 4) + 4 * n_other
 RTOL_D = 1e-10
 RTOL_COUPLED = 1e-11
 RTOL_BATCH = 1e-12           # fracture continua: rtol 1e-10 leaves errors up to ~3e-8
@@ -300,10 +312,11 @@ def main():
     L, Ncell = w.L, w.nx * w.ny
     cells_steps = L * Ncell * args.steps
 
-    def opts_for(rtol, precision=0):
+    def opts_for(rtol, precision=0, inner_form=0):
         o = mc.mc_default_opts()
         o.rtol = rtol
         o.precision = precision
+        o.inner_form = inner_form
         return o
 
     def timed_run(scheme, opts):
@@ -350,16 +363,20 @@ def main():
                              "ms_per_step": 1e3 * cdev / args.steps, "rtol": RTOL_COUPLED,
                              "pcg_iterations_per_step": float(np.mean(cits)),
                              "decoupled_speedup": cdev / dev_time}
-        for name, prec in (("fp32_ir", 1), ("bf16t_ir", 2)):
-            pdev, pits, psw = timed_run("D", opts_for(RTOL_D, prec))
+        for name, prec, form in (("fp32_ir", 1, 0), ("bf16t_ir", 2, 0),
+                                 ("fp32_ir_two_reductions", 1, 1)):
+            pdev, pits, psw = timed_run("D", opts_for(RTOL_D, prec, form))
             pci = float(sum(pits)) * Ncell
-            gbs = BYTES_PER_CELL_IT_32 * pci / pdev / 1e9
+            bpc = inner_bytes_per_cell_it(prec, form)
+            gbs = bpc * pci / pdev / 1e9
             extras[name] = {"value": ws * cells_steps / pdev, "unit": "continuum-cell updates/s",
                             "ms_per_step": 1e3 * pdev / args.steps, "rtol": RTOL_D,
+                            "inner_form": "single reduction" if form == 0 else "two reductions",
                             "inner_iterations_per_step": float(np.mean(pits)),
                             "ir_sweeps_per_step": psw / args.steps,
                             "roofline_inner": {"bound": "hbm", "achieved": gbs, "peak": hbm,
-                                               "unit": "GB/s", "frac": gbs / hbm}}
+                                               "unit": "GB/s", "frac": gbs / hbm,
+                                               "bytes_per_cell_iteration": bpc}}
 
     e2e = None
     ctx = mc.Context.from_workload(w, opts=opts_for(RTOL_D), stream=stream)

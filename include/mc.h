@@ -67,6 +67,11 @@ typedef struct {
 
 enum { MC_PREC_FP64 = 0, MC_PREC_FP32_IR = 1, MC_PREC_BF16T_IR = 2 };
 enum { MC_PRECOND_JACOBI = 0 };
+/* Inner FP32 PCG of the IR forms: single-reduction (Chronopoulos-Gear)
+   recurrences, one grid-wide reduction per iteration, or the textbook
+   (Hestenes-Stiefel) recurrences with two. Both are the Jacobi PCG of
+   Section 3.3's per-continuum systems in exact arithmetic. */
+enum { MC_INNER_SINGLE_REDUCTION = 0, MC_INNER_TWO_REDUCTIONS = 1 };
 enum { MC_SCHEME_COUPLED = -1, MC_SCHEME_D = 0, MC_SCHEME_L = 1, MC_SCHEME_U = 2 };
 
 typedef struct {
@@ -90,6 +95,8 @@ typedef struct {
   int64_t spin_limit;  /* polls of a grid barrier before MC_E_TIMEOUT */
   int32_t blocks;      /* persistent CTAs (0: one per SM x occupancy) */
   int32_t threads;     /* threads per CTA (0: default 512) */
+  int32_t inner_form;  /* MC_INNER_* (IR forms; default single reduction) */
+  int32_t reserved;    /* 0 */
 } mc_opts;
 
 typedef struct {

@@ -14,6 +14,7 @@ MC_MAX_CONTINUA = 4
 MC_OK, MC_E_ARG, MC_E_ALLOC, MC_E_CUDA, MC_E_NOCONV, MC_E_TIMEOUT, MC_E_STATE, MC_E_BREAKDOWN = range(8)
 MC_PREC_FP64, MC_PREC_FP32_IR, MC_PREC_BF16T_IR = 0, 1, 2
 MC_PRECOND_JACOBI = 0
+MC_INNER_SINGLE_REDUCTION, MC_INNER_TWO_REDUCTIONS = 0, 1
 MC_SCHEME_COUPLED, MC_SCHEME_D, MC_SCHEME_L, MC_SCHEME_U = -1, 0, 1, 2
 
 dp = C.POINTER(C.c_double)
@@ -29,6 +30,7 @@ class mc_opts(C.Structure):
         ("precision", C.c_int32), ("precond", C.c_int32), ("max_iter", C.c_int32),
         ("ir_max", C.c_int32), ("rtol", C.c_double), ("inner_rtol", C.c_double),
         ("spin_limit", C.c_int64), ("blocks", C.c_int32), ("threads", C.c_int32),
+        ("inner_form", C.c_int32), ("reserved", C.c_int32),
     ]
 
 

@@ -82,6 +82,10 @@ mc_status check_opts(const mc_opts* o, std::string* why) {
   if (o->spin_limit < 1) { *why = "spin_limit < 1"; return MC_E_ARG; }
   if (o->threads != 0 && o->threads != 512) { *why = "threads must be 0 or 512"; return MC_E_ARG; }
   if (o->blocks < 0) { *why = "blocks < 0"; return MC_E_ARG; }
+  if (o->inner_form != MC_INNER_SINGLE_REDUCTION && o->inner_form != MC_INNER_TWO_REDUCTIONS) {
+    *why = "inner_form";
+    return MC_E_ARG;
+  }
   return MC_OK;
 }
 
@@ -173,6 +177,7 @@ mc_status mc_default_opts(mc_opts* o) {
   o->spin_limit = 2000000;
   o->blocks = 0;
   o->threads = 0;
+  o->inner_form = MC_INNER_SINGLE_REDUCTION;
   return MC_OK;
 }
 

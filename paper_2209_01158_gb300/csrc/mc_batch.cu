@@ -136,6 +136,7 @@ BatchParams make_params(const mc_batch* b, int scheme) {
   bp.inner_rtol = b->opts.inner_rtol;
   bp.max_iter = b->opts.max_iter;
   bp.ir_max = b->opts.ir_max;
+  bp.inner_form = b->opts.inner_form;
   bp.spin_limit = b->opts.spin_limit;
   bp.ctrl = b->d_ctrl;
   bp.abort_word = b->d_abort;
@@ -355,7 +356,8 @@ mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t n, const mc_opts* opts, m
   if (opts->precision != MC_PREC_FP32_IR && opts->precision != MC_PREC_BF16T_IR)
     return berr(nullptr, MC_E_ARG, "the batched form needs precision MC_PREC_FP32_IR or MC_PREC_BF16T_IR");
   if (opts->max_iter < 1 || !(opts->rtol > 0.0) || !(opts->rtol < 1.0) || opts->spin_limit < 1 ||
-      opts->blocks < 0 || opts->ir_max < 0 || !(opts->inner_rtol > 0.0) || !(opts->inner_rtol < 1.0))
+      opts->blocks < 0 || opts->ir_max < 0 || !(opts->inner_rtol > 0.0) || !(opts->inner_rtol < 1.0) ||
+      (opts->inner_form != MC_INNER_SINGLE_REDUCTION && opts->inner_form != MC_INNER_TWO_REDUCTIONS))
     return berr(nullptr, MC_E_ARG, "opts out of range");
   for (int i = 0; i < n; ++i)
     if (!ctxs[i]) return berr(nullptr, MC_E_ARG, "context " + std::to_string(i) + " is NULL");

@@ -55,10 +55,14 @@ struct StepParams {
 };
 
 // TMA descriptors of the arrays the stencil phase reads through tiles.
+// The precision form's single-reduction inner solve also reads a second
+// residual buffer (q) and the double-buffered w = A M r through tiles.
 struct TmaMaps {
   CUtensorMap r[MCL];
   CUtensorMap P[2][MCL];
   CUtensorMap invd[MCL];
+  CUtensorMap q[MCL];
+  CUtensorMap w[2][MCL];
 };
 
 // Extra state of the precision form (FP32 inner PCG in FP64 refinement).
@@ -68,6 +72,8 @@ struct IrParams {
   float* P32[2][MCL];
   float* q32[MCL];
   float* d32[MCL];
+  float* w32[2][MCL];            // single-reduction form: w = A M r (double-buffered)
+  float* p32[MCL];               // single-reduction form: search direction
   const float* invd32[MCL];
   const void* TElo[MCL];         // float or bf16 transmissibilities
   const void* TNlo[MCL];
@@ -75,6 +81,7 @@ struct IrParams {
   float dcf[MCL];                // its constant value otherwise
   double inner_rtol;
   int ir_max;
+  int inner_form;                // MC_INNER_*
   int* ir_sweeps;
   unsigned* abort_word;          // raised by a timed-out barrier; every barrier polls it
 };
@@ -105,6 +112,7 @@ struct BatchParams {
   double rtol;
   double inner_rtol;
   int max_iter, ir_max;
+  int inner_form;                // MC_INNER_*
   long long spin_limit;
   unsigned* ctrl;                // [0] queue; team t: u64 barrier count at 32(t+1),
                                  // ticket at 32(t+1)+4 (zeroed before each launch)
@@ -144,6 +152,8 @@ struct mc_ctx {
   float* P32[2][MCL] = {};
   float* q32[MCL] = {};
   float* d32[MCL] = {};
+  float* w32[2][MCL] = {};
+  float* p32[MCL] = {};
   float* invd32[MCL] = {};
   float* TElo32[MCL] = {};         // FP32 copies, or BF16 in their first half
   float* TNlo32[MCL] = {};

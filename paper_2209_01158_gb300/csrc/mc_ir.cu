@@ -47,6 +47,7 @@ constexpr int NT = 512;
 constexpr int RPT = NT / TX;            // 8 tile rows per pass of the CTA
 constexpr int CPT = TY / RPT;           // 2 own cells per thread
 constexpr int NST = 6;
+constexpr int NBOX = 4;                 // box slots per ring stage (3 used by the two-reduction form)
 constexpr int KM = MC_KMAX_ALLOC;
 
 __device__ __forceinline__ float tload(const float* p, long long i) { return __ldg(p + i); }
@@ -143,6 +144,7 @@ __device__ __forceinline__ double dcell(const StepParams& sp, int a, long long i
 // once per thread (FP64 issue slots are scarce on this GPU).
 struct InnerScal {
   double rr0[MCL], rz[MCL], rr[MCL], rmin[MCL], rck[MCL];
+  double gam[MCL], alp[MCL];  // single-reduction form: (r, M r) and alpha of the last pass
   float alpha[MCL], beta[MCL];
   int its[MCL];
   unsigned act;
@@ -153,12 +155,248 @@ struct InnerScal {
 struct Sm {
   Team team;
   InnerScal* sc;
-  float* box;      // [NST][3][ABOX]
+  float* box;      // [NST][NBOX][ABOX]
   float* pn;       // [PN]
   double* red;     // [NT/32][KM]
   double* res;     // [KM]
   uint64_t* bar;   // [NST]
 };
+
+// Inner FP32 PCG with ONE grid-wide reduction per iteration: the
+// Chronopoulos-Gear recurrences of Jacobi PCG (u = M r, w = A u, s = A p
+// carried by recurrence). In exact arithmetic they produce the iterates of
+// textbook PCG on A d = r0; the two inner products of an iteration,
+// gamma = (r, u) and delta = (w, u), are formed after the same pass, and
+// alpha follows from delta - beta gamma / alpha_prev = (p, A p).
+//
+// One pass per iteration i, tile by tile with a one-cell halo:
+//   s_i = w_i + beta_i s_{i-1},  r_{i+1} = r_i - alpha_i s_i   (tile + halo)
+//   u_{i+1} = M r_{i+1}                                         (tile + halo)
+//   p_i = M r_i + beta_i p_{i-1},  d += alpha_i p_i             (tile)
+//   w_{i+1} = A u_{i+1},  (r,r), (r,u), (w,u) of i+1             (tile)
+// The halo values are recomputed from the previous pass's vectors (the same
+// fused multiply-adds as their owner tile, so both copies agree bit for bit),
+// which is what lets the stencil of w_{i+1} follow the update without a
+// second grid barrier. r, s and w are double-buffered (buffer `cur` is read
+// through TMA, `cur ^ 1` written); p and d are only touched at their own cells
+// and stay in place. Pass -1 runs with alpha = beta = 0 on s = w = p = 0 and
+// forms w_0 = A M r_0 and the first inner products.
+//
+// Returns false only when the launch must stop (barrier timeout / abort);
+// convergence, the progress window and breakdown end a continuum's solve and
+// leave d consistent with the last residual formed.
+template <int L, typename TT>
+__device__ bool inner_single(const IrParams& ip, const TmaMaps& maps, unsigned active, Sm& sm,
+                             uint32_t& phb, int& slot, int inner_cap) {
+  const StepParams& sp = ip.sp;
+  const int nx = sp.nx, ny = sp.ny, pitch = sp.pitch;
+  const int tid = threadIdx.x;
+  const Team tm = sm.team;
+  const double in2 = ip.inner_rtol * ip.inner_rtol;
+  InnerScal& S = *sm.sc;
+  if (tid == 0) {
+    for (int a = 0; a < L; ++a) {
+      S.alpha[a] = 0.f;
+      S.beta[a] = 0.f;
+    }
+    S.act = active;
+    S.iok = 0;
+    S.brk = 0;
+  }
+  __syncthreads();
+  unsigned act = active;
+  int cur = 0;
+  int it = -1;
+  const int tiles = sp.tiles_x * sp.tiles_y;
+  const int lx = tid % TX, ly = tid / TX;
+  while (act) {
+    if (it >= inner_cap) break;
+    int alist[L];
+    int nact = 0;
+#pragma unroll
+    for (int a = 0; a < L; ++a) if (act & (1u << a)) alist[nact++] = a;
+    // per continuum: (r, r), (r, u), (w, u) of the new residual
+    float dots[3 * L];
+#pragma unroll
+    for (int k = 0; k < 3 * L; ++k) dots[k] = 0.f;
+    const int ntask = nact * tiles;
+    auto issue = [&](int task, int s) {
+      const int w = task / tiles, tt = task - w * tiles;
+      int a0 = 0;
+#pragma unroll
+      for (int k = 0; k < L; ++k) if (k == w) a0 = alist[k];
+      const int bx0 = (tt % sp.tiles_x) * TX - HOFF;
+      const int by0 = (tt / sp.tiles_x) * TY - 1;
+      uint64_t* bar = sm.bar + s;
+      fence_proxy_async();
+      mbar_expect_tx(bar, 4 * BOX_BYTES);
+      float* base = sm.box + (size_t)s * NBOX * ABOX;
+      tma_load_2d(base, cur ? &maps.q[a0] : &maps.r[a0], bx0, by0, bar);
+      tma_load_2d(base + ABOX, &maps.P[cur][a0], bx0, by0, bar);
+      tma_load_2d(base + 2 * ABOX, &maps.w[cur][a0], bx0, by0, bar);
+      tma_load_2d(base + 3 * ABOX, &maps.invd[a0], bx0, by0, bar);
+    };
+    const int G = tm.size;
+    int tk = tm.rank, k = 0;
+    unsigned pend = 0;
+#pragma unroll
+    for (int j = 0; j < NST - 1; ++j) {
+      const int tj = tk + j * G;
+      if (tj < ntask) {
+        if (tid == 0) issue(tj, j);
+        pend |= 1u << j;
+      }
+    }
+    bool tma_ok = true;
+    for (; tk < ntask; tk += G, ++k) {
+      const int s = k % NST;
+      {
+        const int tn = tk + (NST - 1) * G, sn = (k + NST - 1) % NST;
+        if (tn < ntask) {
+          if (tid == 0) issue(tn, sn);
+          pend |= 1u << sn;
+        }
+      }
+      const int w = tk / tiles, tt = tk - w * tiles;
+      int a0 = 0;
+#pragma unroll
+      for (int kk = 0; kk < L; ++kk) if (kk == w) a0 = alist[kk];
+      const int x0 = (tt % sp.tiles_x) * TX, y0 = (tt / sp.tiles_x) * TY;
+      const int gx = x0 + lx;
+      const TT* TE = static_cast<const TT*>(ip.TElo[a0]);
+      const TT* TN = static_cast<const TT*>(ip.TNlo[a0]);
+      float te[CPT], tw[CPT], tn[CPT], ts[CPT], dc[CPT], pold[CPT], dold[CPT];
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int gy = y0 + ly + RPT * j;
+        const long long i = (long long)gy * pitch + gx;
+        te[j] = tw[j] = tn[j] = ts[j] = dc[j] = pold[j] = dold[j] = 0.f;
+        if (gx < nx && gy < ny) {
+          te[j] = tload(TE, i);
+          tn[j] = tload(TN, i);
+          if (gx > 0) tw[j] = tload(TE, i - 1);
+          if (gy > 0) ts[j] = tload(TN, i - pitch);
+          dc[j] = ip.dc32[a0] ? __ldg(ip.dc32[a0] + i) : ip.dcf[a0];
+          pold[j] = __ldcg(ip.p32[a0] + i);
+          dold[j] = __ldcg(ip.d32[a0] + i);
+        }
+      }
+      if (!mbar_wait(sm.bar + s, (phb >> s) & 1u, sp.spin_limit)) {
+        if (tid == 0) grid_raise_abort(irbar(ip, tm), (int)MC_E_TIMEOUT);
+        tma_ok = false;
+        break;
+      }
+      phb ^= 1u << s;
+      pend &= ~(1u << s);
+      const float* bR = sm.box + (size_t)s * NBOX * ABOX;
+      const float* bS = bR + ABOX;
+      const float* bW = bR + 2 * ABOX;
+      const float* bD = bR + 3 * ABOX;
+      const float al = S.alpha[a0], bt = S.beta[a0];
+      // u_{i+1} = M (r_i - alpha (w_i + beta s_{i-1})) on the 66 x 18 region
+      for (int e = tid; e < PN; e += NT) {
+        const int ry = e / PX, rx = e - ry * PX;
+        const int b = ry * BX + rx + (HOFF - 1);
+        const float sn = __fmaf_rn(bt, bS[b], bW[b]);
+        const float rn = __fmaf_rn(-al, sn, bR[b]);
+        sm.pn[e] = __fmul_rn(bD[b], rn);
+      }
+      __syncthreads();
+      float* rN = cur ? ip.r32[a0] : ip.q32[a0];
+      float* sN = ip.P32[cur ^ 1][a0];
+      float* wN = ip.w32[cur ^ 1][a0];
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int lyj = ly + RPT * j;
+        const int gy = y0 + lyj;
+        if (gx >= nx || gy >= ny) continue;
+        const long long i = (long long)gy * pitch + gx;
+        const int c = (lyj + 1) * PX + lx + 1;
+        const int b = (lyj + 1) * BX + lx + HOFF;
+        const float sn = __fmaf_rn(bt, bS[b], bW[b]);
+        const float rn = __fmaf_rn(-al, sn, bR[b]);
+        const float uc = sm.pn[c];
+        const float pv = __fmaf_rn(bt, pold[j], __fmul_rn(bD[b], bR[b]));
+        const float dv = __fmaf_rn(al, pv, dold[j]);
+        const float wv = dc[j] * uc + te[j] * (uc - sm.pn[c + 1]) + tw[j] * (uc - sm.pn[c - 1]) +
+                         tn[j] * (uc - sm.pn[c + PX]) + ts[j] * (uc - sm.pn[c - PX]);
+        rN[i] = rn;
+        sN[i] = sn;
+        wN[i] = wv;
+        ip.p32[a0][i] = pv;
+        ip.d32[a0][i] = dv;
+#pragma unroll
+        for (int kk = 0; kk < L; ++kk)
+          if (kk == a0) {
+            dots[kk] += rn * rn;
+            dots[L + kk] += rn * uc;
+            dots[2 * L + kk] += wv * uc;
+          }
+      }
+      __syncthreads();
+    }
+    if (!tma_ok) {
+      for (int st = 0; st < NST; ++st)
+        if (pend & (1u << st)) mbar_wait(sm.bar + st, (phb >> st) & 1u, 1LL << 24);
+      return false;
+    }
+    store_part_f<3 * L>(dots, qbits(act, L, 3), sm.box, sp.partials, slot, tm);
+    if (!gsync(ip, tm)) return false;
+    sum_totals<3 * L>(sp.partials, slot, sm.res, tm);
+    slot ^= 1;
+    if (tid == 0) {
+      unsigned a_act = act;
+      for (int a = 0; a < L; ++a) {
+        const unsigned bit = 1u << a;
+        if (!(act & bit)) continue;
+        const double rr = sm.res[a], gam = sm.res[L + a], del = sm.res[2 * L + a];
+        if (it < 0) {
+          // pass -1: r_0, u_0 = M r_0, w_0 = A u_0; alpha_0 = gamma / delta
+          S.rr0[a] = S.rr[a] = S.rmin[a] = S.rck[a] = rr;
+          if (!(rr > 0.0) || !(gam > 0.0) || !(del > 0.0) || !isfinite(gam) || !isfinite(del)) {
+            a_act &= ~bit;
+            continue;
+          }
+          S.gam[a] = gam;
+          S.alp[a] = gam / del;
+          S.alpha[a] = (float)S.alp[a];
+          S.beta[a] = 0.f;
+          continue;
+        }
+        S.rr[a] = rr;
+        S.its[a] += 1;
+        if (!(rr > in2 * S.rr0[a])) S.iok |= bit;
+        if (!(rr > in2 * S.rr0[a]) || !isfinite(rr)) {
+          a_act &= ~bit;
+          continue;
+        }
+        // FP32 progress test, as in the two-reduction form: the smallest
+        // residual seen must halve in every window of 2048 iterations
+        if (rr < S.rmin[a]) S.rmin[a] = rr;
+        if (((it + 1) & 2047) == 0) {
+          if (!(S.rmin[a] < 0.25 * S.rck[a])) a_act &= ~bit;
+          S.rck[a] = S.rmin[a];
+        }
+        const double be = gam / S.gam[a];
+        const double den = del - be * gam / S.alp[a];
+        if (!(gam > 0.0) || !(den > 0.0) || !isfinite(den)) {
+          a_act &= ~bit;  // breakdown: keep what the sweep reached
+          continue;
+        }
+        S.gam[a] = gam;
+        S.alp[a] = gam / den;
+        S.alpha[a] = (float)S.alp[a];
+        S.beta[a] = (float)be;
+      }
+      S.act = a_act;
+    }
+    __syncthreads();
+    act = S.act;
+    cur ^= 1;
+    ++it;
+  }
+  return true;
+}
 
 // One solve of the continua in `mask` (all at once for D; one for L/U).
 template <int L, typename TT>
@@ -174,6 +412,7 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
   const bool lag_prev = sp.scheme == MC_SCHEME_D;
   const double rtol2 = sp.rtol * sp.rtol;
   const double in2 = ip.inner_rtol * ip.inner_rtol;
+  const bool single = ip.inner_form == MC_INNER_SINGLE_REDUCTION;
   double bb[L], rr_prev[L], rr_last[L];
 #pragma unroll
   for (int a = 0; a < L; ++a) bb[a] = rr_prev[a] = rr_last[a] = 0.0;
@@ -287,18 +526,44 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
         if (go) {
           const double rv = __ldcg(sp.r[a] + i) - c * dcell(sp, a, i);
           const float r32 = (float)rv;
-          const float z = __ldg(ip.invd32[a] + i) * r32;
           ip.r32[a][i] = r32;
           ip.d32[a][i] = 0.0f;
-          ip.P32[0][a][i] = z;
-          acc2[a] += (double)r32 * (double)r32;
-          acc2[L + a] += (double)r32 * (double)z;
+          if (single) {
+            // s_{-1} = w_{-1} = p_{-1} = 0: the first pass of the
+            // single-reduction loop then forms w_0 = A M r_0
+            ip.P32[0][a][i] = 0.0f;
+            ip.w32[0][a][i] = 0.0f;
+            ip.p32[a][i] = 0.0f;
+          } else {
+            const float z = __ldg(ip.invd32[a] + i) * r32;
+            ip.P32[0][a][i] = z;
+            acc2[a] += (double)r32 * (double)r32;
+            acc2[L + a] += (double)r32 * (double)z;
+          }
         }
       }
     }
     active = inner;
     if (!active) break;
     ++sweeps;
+    // The inner solve ends at inner_rtol, when FP32 CG stops making progress
+    // (the window test), or at a cap of 16 max(nx, ny) iterations within
+    // [2048, 16384] (and max_iter). The cap has two sides: on a fracture
+    // continuum (k 1e4 in thin connected networks, 1e-2 around them)
+    // Jacobi-PCG needs about 10 n iterations for the 1e-3 reduction, and
+    // cutting that short multiplies the total work; but a very long FP32 run
+    // drifts (its recursive residual keeps falling while the true one does
+    // not: 100000-iteration sweeps at 4096^2 and contrast 1e5 gained
+    // nothing), so the FP64 sweep restarts it.
+    int inner_cap = 16 * (nx > ny ? nx : ny);
+    if (inner_cap < 2048) inner_cap = 2048;
+    if (inner_cap > 16384) inner_cap = 16384;
+    if (inner_cap > sp.max_iter) inner_cap = sp.max_iter;
+    if (single) {
+      if (!gsync(ip, tm)) return false;
+      if (!inner_single<L, TT>(ip, maps, active, sm, phb, slot, inner_cap)) return false;
+      iok = sm.sc->iok;
+    } else {
     store_part<2 * L>(acc2, qbits(inner, L, 2), sm.box, sp.partials, slot, tm);
     if (!gsync(ip, tm)) return false;
     sum_totals<2 * L>(sp.partials, slot, sm.res, tm);
@@ -324,19 +589,6 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
     int it = 0;
     const int tiles = sp.tiles_x * sp.tiles_y;
     const int lx = tid % TX, ly = tid / TX;
-    // The inner solve ends at inner_rtol, when FP32 CG stops making progress
-    // (the window test below), or at a cap of 16 max(nx, ny) iterations
-    // within [2048, 16384] (and max_iter). The cap has two sides: on a
-    // fracture continuum (k 1e4 in thin connected networks, 1e-2 around
-    // them) Jacobi-PCG needs about 10 n iterations for the 1e-3 reduction,
-    // and cutting that short multiplies the total work; but a very long
-    // FP32 run drifts (its recursive residual keeps falling while the true
-    // one does not: 100000-iteration sweeps at 4096^2 and contrast 1e5
-    // gained nothing), so the FP64 sweep restarts it.
-    int inner_cap = 16 * (nx > ny ? nx : ny);
-    if (inner_cap < 2048) inner_cap = 2048;
-    if (inner_cap > 16384) inner_cap = 16384;
-    if (inner_cap > sp.max_iter) inner_cap = sp.max_iter;
     while (act) {
       if (it >= inner_cap) break;  // the outer loop measures what was reached
       int alist[L];
@@ -357,7 +609,7 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
         uint64_t* bar = sm.bar + s;
         fence_proxy_async();
         mbar_expect_tx(bar, 3 * BOX_BYTES);
-        float* base = sm.box + (size_t)s * 3 * ABOX;
+        float* base = sm.box + (size_t)s * NBOX * ABOX;
         tma_load_2d(base, &maps.r[a0], bx0, by0, bar);
         tma_load_2d(base + ABOX, &maps.P[cur][a0], bx0, by0, bar);
         tma_load_2d(base + 2 * ABOX, &maps.invd[a0], bx0, by0, bar);
@@ -412,7 +664,7 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
         }
         phb ^= 1u << s;
         pend &= ~(1u << s);
-        const float* base = sm.box + (size_t)s * 3 * ABOX;
+        const float* base = sm.box + (size_t)s * NBOX * ABOX;
         const float bt = S.beta[a0];
         for (int e = tid; e < PN; e += NT) {
           const int ry = e / PX, rx = e - ry * PX;
@@ -527,6 +779,7 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
       cur ^= 1;
     }
     iok = S.iok;
+    }
     // ---- 4. x += d (FP64) -------------------------------------------------------
 #pragma unroll
     for (int a = 0; a < L; ++a) {
@@ -568,7 +821,7 @@ __device__ __forceinline__ void carve(Sm& sm, unsigned char* smem_raw, InnerScal
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   sm.sc = sc;
   sm.box = reinterpret_cast<float*>(base);
-  sm.pn = sm.box + NST * 3 * ABOX;
+  sm.pn = sm.box + NST * NBOX * ABOX;
   sm.red = reinterpret_cast<double*>(sm.pn + ((PN + 1) / 2) * 2);
   sm.res = sm.red + (NT / 32) * KM;
   sm.bar = reinterpret_cast<uint64_t*>(sm.res + KM);
@@ -678,6 +931,7 @@ __global__ void __launch_bounds__(NT, 1) ir_batch_kernel(const __grid_constant__
       sp.relres = rec->relres;
       s_ip.inner_rtol = bp.inner_rtol;
       s_ip.ir_max = bp.ir_max;
+      s_ip.inner_form = bp.inner_form;
       s_ip.ir_sweeps = &rec->ir_sweeps;
       s_ip.abort_word = bp.abort_word;
       s_flag = __ldcg(&rec->status) != 0;
@@ -720,7 +974,7 @@ __global__ void __launch_bounds__(NT, 1) ir_batch_kernel(const __grid_constant__
 
 template <int L, typename TT>
 size_t ir_smem() {
-  return (size_t)NST * 3 * ABOX * 4 + (size_t)((PN + 1) / 2) * 2 * 4 +
+  return (size_t)NST * NBOX * ABOX * 4 + (size_t)((PN + 1) / 2) * 2 * 4 +
          (size_t)((NT / 32) * KM + KM) * 8 + NST * 8 + 128;
 }
 
@@ -794,6 +1048,9 @@ cudaError_t mc_ir_prepare(mc_ctx* ctx, int bf16) {
         if ((e = mc_alloc(ctx, (void**)&ctx->P32[1][a], fb4)) != cudaSuccess) return e;
         if ((e = mc_alloc(ctx, (void**)&ctx->q32[a], fb4)) != cudaSuccess) return e;
         if ((e = mc_alloc(ctx, (void**)&ctx->d32[a], fb4)) != cudaSuccess) return e;
+        if ((e = mc_alloc(ctx, (void**)&ctx->w32[0][a], fb4)) != cudaSuccess) return e;
+        if ((e = mc_alloc(ctx, (void**)&ctx->w32[1][a], fb4)) != cudaSuccess) return e;
+        if ((e = mc_alloc(ctx, (void**)&ctx->p32[a], fb4)) != cudaSuccess) return e;
         if ((e = mc_alloc(ctx, (void**)&ctx->invd32[a], fb4)) != cudaSuccess) return e;
         if ((e = mc_alloc(ctx, (void**)&ctx->TElo32[a], fb4)) != cudaSuccess) return e;
         if ((e = mc_alloc(ctx, (void**)&ctx->TNlo32[a], fb4)) != cudaSuccess) return e;
@@ -813,6 +1070,11 @@ cudaError_t mc_ir_prepare(mc_ctx* ctx, int bf16) {
                              ctx->nx, ctx->ny, ctx->pitch, bx, by)) != cudaSuccess) return e;
       if ((e = mc_encode_map(&ctx->maps32.invd[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->invd32[a],
                              ctx->nx, ctx->ny, ctx->pitch, bx, by)) != cudaSuccess) return e;
+      if ((e = mc_encode_map(&ctx->maps32.q[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->q32[a],
+                             ctx->nx, ctx->ny, ctx->pitch, bx, by)) != cudaSuccess) return e;
+      for (int h = 0; h < 2; ++h)
+        if ((e = mc_encode_map(&ctx->maps32.w[h][a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ctx->w32[h][a],
+                               ctx->nx, ctx->ny, ctx->pitch, bx, by)) != cudaSuccess) return e;
     }
     ctx->lo_kind = 1 + bf16;
   }
@@ -831,6 +1093,9 @@ void mc_ir_fill(const mc_ctx* ctx, const StepParams& sp_in, IrParams* ip) {
     ip->P32[1][a] = ctx->P32[1][a];
     ip->q32[a] = ctx->q32[a];
     ip->d32[a] = ctx->d32[a];
+    ip->w32[0][a] = ctx->w32[0][a];
+    ip->w32[1][a] = ctx->w32[1][a];
+    ip->p32[a] = ctx->p32[a];
     ip->invd32[a] = ctx->invd32[a];
     ip->TElo[a] = ctx->TElo32[a];
     ip->TNlo[a] = ctx->TNlo32[a];
@@ -839,6 +1104,7 @@ void mc_ir_fill(const mc_ctx* ctx, const StepParams& sp_in, IrParams* ip) {
   }
   ip->inner_rtol = ctx->opts.inner_rtol;
   ip->ir_max = ctx->opts.ir_max;
+  ip->inner_form = ctx->opts.inner_form;
   ip->ir_sweeps = ctx->dsweeps;
   ip->abort_word = sp_in.bar_gen + 32;
 }

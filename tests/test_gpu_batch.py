@@ -62,9 +62,9 @@ def ref_d4(ws):
     return oracle_runs(ws, 4, "D")
 
 
-@pytest.mark.parametrize("team", [None, 1, 3, 16])
-def test_batch_d_scheme_matches_oracle(mc, ws, ref_d4, team):
-    o = opts(mc)
+@pytest.mark.parametrize("team,inner_form", [(None, 0), (1, 0), (3, 0), (16, 0), (None, 1), (3, 1)])
+def test_batch_d_scheme_matches_oracle(mc, ws, ref_d4, team, inner_form):
+    o = opts(mc, inner_form=inner_form)
     ctxs = [mc.Context.from_workload(w, opts=o) for w in ws]
     b = mc.Batch(ctxs, o, team=team)
     st = b.step("D", 4)

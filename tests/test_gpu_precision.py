@@ -24,10 +24,11 @@ def mc():
     return m
 
 
-def run(mc, w, scheme, nsteps, precision, rtol=1e-10):
+def run(mc, w, scheme, nsteps, precision, rtol=1e-10, inner_form=0):
     o = mc.mc_default_opts()
     o.precision = precision
     o.rtol = rtol
+    o.inner_form = inner_form
     ctx = mc.Context.from_workload(w, opts=o)
     st = ctx.step(scheme, nsteps)
     p = ctx.get_state()
@@ -35,29 +36,43 @@ def run(mc, w, scheme, nsteps, precision, rtol=1e-10):
     return p, st
 
 
+# inner_form 0: single-reduction (Chronopoulos-Gear) inner PCG, the default;
+# 1: the two-reduction textbook recurrences
+@pytest.mark.parametrize("inner_form", [0, 1])
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("scheme", ["D", "L", "U"])
-def test_three_continuum_ragged(mc, precision, scheme):
+def test_three_continuum_ragged(mc, precision, scheme, inner_form):
     w = mi.triple_1024(n=100)
-    p, st = run(mc, w, scheme, 6, precision)
+    p, st = run(mc, w, scheme, 6, precision, inner_form=inner_form)
     ref = from_workload(w).run(w.p0, w.F, 6, scheme)
     assert metrics.rel_l2(ref, p) <= MIXED_TOL
     assert st["ir_sweeps"] > 0
 
 
+@pytest.mark.parametrize("inner_form", [0, 1])
 @pytest.mark.parametrize("precision", [1, 2])
-def test_dual_64_full_run(mc, precision):
+def test_dual_64_full_run(mc, precision, inner_form):
     w = mi.dual_64()
-    p, st = run(mc, w, "D", w.nsteps, precision)
+    p, st = run(mc, w, "D", w.nsteps, precision, inner_form=inner_form)
     ref = from_workload(w).run(w.p0, w.F, w.nsteps, "D")
     assert metrics.rel_l2(ref, p) <= MIXED_TOL
 
 
-def test_fracture_instance_per_cell_exchange(mc):
+@pytest.mark.parametrize("inner_form", [0, 1])
+def test_fracture_instance_per_cell_exchange(mc, inner_form):
     w = mi.fracture_instance(4007, n=72, L=3)
-    p, st = run(mc, w, "D", 5, 2)
+    p, st = run(mc, w, "D", 5, 2, inner_form=inner_form)
     ref = from_workload(w).run(w.p0, w.F, 5, "D")
     assert metrics.rel_l2(ref, p) <= MIXED_TOL
+
+
+def test_inner_form_out_of_range_rejected(mc):
+    w = mi.dual_64(n=16)
+    o = mc.mc_default_opts()
+    o.precision = 1
+    o.inner_form = 2
+    with pytest.raises(Exception):
+        mc.Context.from_workload(w, opts=o)
 
 
 def test_coupled_scheme_rejects_precision_form(mc):
