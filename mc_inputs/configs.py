@@ -33,6 +33,8 @@ class Workload:
     F: List[np.ndarray]                     # L arrays (ny, nx)
     p0: List[np.ndarray]                    # L arrays (ny, nx)
     sigma_cell: Dict[Tuple[int, int], np.ndarray] = field(default_factory=dict)
+    # implicit wells: continuum -> (W = q_w |cell| per cell, p_w per cell)
+    wells: Dict[int, Tuple[np.ndarray, np.ndarray]] = field(default_factory=dict)
     coarse: Optional[Tuple[int, int, int]] = None   # (ncx, ncy, layers)
     seed: Optional[int] = None
 
@@ -171,6 +173,65 @@ def nlmc_1024(n=1024, seed=5000, ncoarse=32, layers=2, nsteps=200):
     return w
 
 
+def _box_cells(n, x0, x1, y0, y1):
+    """Cells whose centres lie in [x0, x1] x [y0, y1] (boolean (n, n))."""
+    c = (np.arange(n) + 0.5) / n
+    return (((c[None, :] >= x0) & (c[None, :] <= x1)) &
+            ((c[:, None] >= y0) & (c[:, None] <= y1)))
+
+
+def paper_wells(L=2, n=200, seed=None, nsteps=50, qw=1e5, pw=1.2):
+    """A workload shaped like the paper's 2C / 3C experiments (Section 5):
+    p^0 = 1 in every continuum, T = 0.002 in 50 steps (tau = 4e-5), wells of
+    index q_w = 1e5 and pressure p_w = 1.2 in the fracture cells of the boxes
+    [0.1, 0.15]^2 and [0.6, 0.65] x [0.85, 0.9], no other source.
+
+    2C: matrix c = 0.1, k = 1; fracture c = 1, k = 1e6.
+    3C: matrix c = 0.05, k = 1e-3; natural fractures c = 0.1, k = 1;
+        hydraulic fractures c = 1, k = 1e6.
+    The paper's 25-line geometry exists only as a figure: 25 seeded random
+    segments stand in for it (centre U[0,1]^2, length U[0.05, 0.5], angle
+    U[0, pi)), rasterised as in `fracture_instance` (crossed cells get the
+    fracture k, the others 1e-2; fracture exchange sigma_i = 10 l_i / h with
+    every other continuum; matrix / natural-fracture exchange 5). A box with
+    no fracture cell gets its well at the fracture cell nearest its centre.
+    W = q_w |cell| in the well cells.
+    """
+    if L not in (2, 3):
+        raise ValueError("L must be 2 or 3")
+    seed = 6000 + L if seed is None else seed
+    rng = np.random.default_rng(seed)
+    ell = segment_lengths(random_segments(rng, 25, 25), n, n)
+    frac = np.where(ell > 0.0, 1e6, 1e-2)
+    sig_f = 10.0 * ell * n
+    if L == 2:
+        k = [np.ones((n, n)), frac]
+        c = np.array([0.1, 1.0])
+        sigma = np.zeros((2, 2))
+        sc = {(0, 1): sig_f}
+    else:
+        k = [np.full((n, n), 1e-3), np.ones((n, n)), frac]
+        c = np.array([0.05, 0.1, 1.0])
+        sigma = _sym(3, {(0, 1): 5.0})
+        sc = {(0, 2): sig_f, (1, 2): sig_f.copy()}
+    W = np.zeros((n, n))
+    jj, ii = np.nonzero(ell > 0.0)
+    for (x0, x1, y0, y1) in ((0.1, 0.15, 0.1, 0.15), (0.6, 0.65, 0.85, 0.9)):
+        box = _box_cells(n, x0, x1, y0, y1) & (ell > 0.0)
+        if not box.any() and jj.size:
+            cx, cy = 0.5 * (x0 + x1) * n - 0.5, 0.5 * (y0 + y1) * n - 0.5
+            m = int(np.argmin((ii - cx) ** 2 + (jj - cy) ** 2))
+            box = np.zeros((n, n), dtype=bool)
+            box[jj[m], ii[m]] = True
+        W[box] = qw / (n * n)
+    tau = 0.002 / nsteps
+    w = Workload("paper%dC_%d" % (L, n), n, n, L, k, c, sigma, tau, nsteps,
+                 [np.zeros((n, n)) for _ in range(L)], [np.ones((n, n)) for _ in range(L)],
+                 sigma_cell=sc, seed=seed)
+    w.wells = {L - 1: (W, np.full((n, n), pw))}
+    return w
+
+
 def scaled(fn, n, **kw):
     """The recipe of `fn` at another grid size (small parity cases)."""
     return fn(n=n, **kw)
@@ -182,5 +243,7 @@ def by_name(name):
         "triple_1024": triple_1024,
         "precision_4096": precision_4096,
         "nlmc_1024": nlmc_1024,
+        "paper_2c": lambda: paper_wells(2),
+        "paper_3c": lambda: paper_wells(3),
     }
     return table[name]()

@@ -15,6 +15,13 @@ Readings of the paper used here:
     with q_alpha_beta,i = sigma_alpha_beta,i |cell| (sigma given per unit
     area; the cell-integrated exchange mirrors the mass and source terms).
   * F_alpha is given already cell-integrated (F = f |cell|).
+  * Well term (Section 5: f_f = q_w (p - p_w) in the well regions). Read as
+    the relaxation q_w (p_w - p) toward the well pressure -- the sign that
+    keeps the problem dissipative -- taken implicitly in p: it adds
+    W = q_w |cell| to the diagonal of the continuum's own block and W p_w to
+    its right-hand side. It is a continuum-local diagonal term, so it sits in
+    A0 of every decoupled scheme. W and p_w are given per cell (W = 0 outside
+    the wells).
 """
 
 import numpy as np
@@ -61,7 +68,7 @@ class FVSystem:
     on tiny grids, row sums of D + Q (mass conservation), symmetry.
     """
 
-    def __init__(self, nx, ny, L, k, c, sigma=None, sigma_cell=None):
+    def __init__(self, nx, ny, L, k, c, sigma=None, sigma_cell=None, wells=None):
         self.nx, self.ny, self.L = int(nx), int(ny), int(L)
         self.N = self.nx * self.ny
         self.h = 1.0 / self.nx
@@ -85,6 +92,18 @@ class FVSystem:
                     s = np.full(self.N, sigma[a, b])
                 self.q[(a, b)] = s * area
                 self.q[(b, a)] = self.q[(a, b)]
+        # wells: W[a] = q_w |cell| per cell and the well pressure pw[a]
+        self.W = [np.zeros(self.N) for _ in range(L)]
+        self.pw = [np.zeros(self.N) for _ in range(L)]
+        for a, (Wa, pwa) in (wells or {}).items():
+            self.W[a] = np.asarray(Wa, dtype=np.float64).ravel().copy()
+            pwa = np.asarray(pwa, dtype=np.float64)
+            self.pw[a] = (pwa.ravel().copy() if pwa.size == self.N
+                          else np.full(self.N, float(pwa)))
+
+    def well_rhs(self, a):
+        """W_a p_w,a: the well term's right-hand side (zero without wells)."""
+        return self.W[a] * self.pw[a]
 
     def exchange_sum(self, a):
         """Diagonal of sum_{beta != a} Q_a,beta."""

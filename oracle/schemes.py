@@ -1,6 +1,8 @@
 """Time schemes on the fine grid, each step solved exactly.
 
   coupled   -- backward Euler, Eq. ct-mc:  (M/tau + A) p^n = M/tau p^{n-1} + F.
+  (With wells, every scheme's own diagonal blocks gain W_a and its
+  right-hand sides W_a p_w,a: the implicit well term, see `fv`.)
   D-scheme  -- Eq. si-mc with A0 = blockdiag(D_a + sum_b Q_ab), A1 = A - A0
                (Section 3.3): every continuum solves
                (M_a/tau + D_a + sum_b Q_ab) p_a^n
@@ -40,14 +42,18 @@ class Oracle:
 
     # -- matrices ---------------------------------------------------------
     def coupled_matrix(self, dtype=np.float64):
-        """M/tau + D + Q over all continua (Eq. ct-mc)."""
-        mt = np.concatenate(self.fv.m) / self.tau
-        return (sp.diags(mt.astype(dtype)) + self.fv.A(dtype)).tocsc()
+        """M/tau + D + Q (+ W, the implicit well term) over all continua
+        (Eq. ct-mc)."""
+        fv = self.fv
+        mt = (np.concatenate(fv.m) / self.tau).astype(dtype) + np.concatenate(fv.W).astype(dtype)
+        return (sp.diags(mt) + fv.A(dtype)).tocsc()
 
     def split_matrix(self, a, dtype=np.float64):
-        """M_a/tau + D_a + sum_b Q_ab: the diagonal block of M/tau + A0."""
+        """M_a/tau + D_a + sum_b Q_ab (+ W_a): the diagonal block of
+        M/tau + A0."""
         fv = self.fv
-        return (sp.diags((fv.m[a] / self.tau).astype(dtype)) + fv.A_block(a, a, dtype)).tocsc()
+        d = (fv.m[a] / self.tau).astype(dtype) + fv.W[a].astype(dtype)
+        return (sp.diags(d) + fv.A_block(a, a, dtype)).tocsc()
 
     # -- direct solves ----------------------------------------------------
     def _factor(self, key):
@@ -72,7 +78,7 @@ class Oracle:
     # -- one step of each scheme -------------------------------------------
     def rhs_coupled(self, p_prev, F):
         fv = self.fv
-        return np.concatenate([fv.m[a] / self.tau * p_prev[a] + F[a]
+        return np.concatenate([fv.m[a] / self.tau * p_prev[a] + F[a] + fv.well_rhs(a)
                                for a in range(fv.L)])
 
     def step_coupled(self, p_prev, F):
@@ -84,7 +90,7 @@ class Oracle:
         """Right-hand side of continuum a: mass term, source and the exchange
         with the other continua, at the newest layer already available."""
         fv = self.fv
-        rhs = fv.m[a] / self.tau * p_prev[a] + F[a]
+        rhs = fv.m[a] / self.tau * p_prev[a] + F[a] + fv.well_rhs(a)
         for b in range(fv.L):
             if b == a:
                 continue
@@ -130,5 +136,6 @@ class Oracle:
 def from_workload(w, refine=3):
     """Oracle and FV system for an `mc_inputs.Workload`."""
     from .fv import FVSystem
-    fv = FVSystem(w.nx, w.ny, w.L, w.k, w.c, w.sigma, w.sigma_cell)
+    fv = FVSystem(w.nx, w.ny, w.L, w.k, w.c, w.sigma, w.sigma_cell,
+                  wells=getattr(w, "wells", None))
     return Oracle(fv, w.tau, refine=refine)
