@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=64,
                     help="instances of the batched fracture workload (seeds 4000..; 0: skip)")
     ap.add_argument("--batch-steps", type=int, default=1, help="timed batched steps")
+    ap.add_argument("--precision-n", type=int, default=4096, help="grid of the precision workload")
+    ap.add_argument("--precision-steps", type=int, default=2, help="timed precision-form steps")
     ap.add_argument("--profile-step", type=int, default=-1, metavar="PRECISION",
                     help="profiling case: one warm-up and one D-scheme step of the workload at "
                          "--n with this precision (0 FP64, 1 FP32 IR, 2 BF16 IR), nothing else")
@@ -235,7 +237,90 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def batched_extra(args, mc, mi, torch, stream, ws):
+def precision_extra(args, mc, mi, torch, stream, ws, hbm):
+    """The precision form on its own workload: two continua on a 4096^2 grid
+    (k2 contrast 1e5), FP32 and BF16 transmissibilities in separate runs, FP64
+    refinement to rtol 1e-10; one warm-up step, then --precision-steps timed
+    steps (CUDA events on the launch stream). At this size one inner
+    iteration moves ~870 MB, far beyond L2, so the inner kernel's bytes come
+    from HBM."""
+    w = mi.precision_4096(n=args.precision_n)
+    Ncell = w.nx * w.ny
+    out = {"workload": "precision_4096: 2 continua, %dx%d, k2 = 1e5 exp(0.5 N), tau = 1/50, "
+                       "D-scheme, refinement rtol %g" % (w.nx, w.ny, RTOL_D)}
+    for name, prec in (("fp32", 1), ("bf16t", 2)):
+        o = mc.mc_default_opts()
+        o.precision = prec
+        o.rtol = RTOL_D
+        ctx = mc.Context.from_workload(w, opts=o, stream=stream)
+        ctx.step("D", 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st = ctx.step("D", args.precision_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) * 1e-3
+        ctx.close()
+        its = float(sum(st["iters"][:w.L]))
+        bpc = inner_bytes_per_cell_it(prec, 0)
+        gbs = bpc * its * Ncell / dt / 1e9
+        out[name] = {"value": ws * w.L * Ncell * args.precision_steps / dt,
+                     "unit": "continuum-cell updates/s",
+                     "s_per_step": dt / args.precision_steps,
+                     "inner_iterations_per_step": its / args.precision_steps,
+                     "ir_sweeps_per_step": st["ir_sweeps"] / args.precision_steps,
+                     "roofline_inner": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                        "frac": gbs / hbm, "bytes_per_cell_iteration": bpc,
+                                        "note": "whole step time (refinement passes included)"}}
+    return out
+
+
+def paper_extra(args, mc, mi, np):
+    """The paper-shaped problems (Section 5): 2C and 3C at 200^2, p^0 = 1,
+    wells at p_w = 1.2 in the fracture boxes, T = 0.002 in 50 steps; FP64,
+    time to solution of the whole run per scheme at rtol 1e-12, and e_h of
+    the decoupled schemes against the coupled run (the paper's Tables 1-2
+    metric, in %). The geometry is a seeded stand-in, so the paper's own
+    numbers are context only."""
+    import time as _t
+    out = {}
+    for L in (2, 3):
+        w = mi.paper_wells(L)
+        res = {}
+        ref = None
+        for scheme in ("coupled", "D", "L", "U"):
+            o = mc.mc_default_opts()
+            o.rtol = RTOL_BATCH
+            ctx = mc.Context.from_workload(w, opts=o)
+            try:
+                ctx.step(scheme, 1)  # warm-up (module load, first launch)
+                ctx.set_state(w.p0)
+                t0 = _t.perf_counter()
+                st = ctx.step(scheme, w.nsteps)
+                dt = _t.perf_counter() - t0
+                p = ctx.get_state()
+                r = {"s": dt, "pcg_iterations_per_step": float(sum(st["iters"][:L])) / w.nsteps}
+                if scheme == "coupled":
+                    ref = p
+                    r["pcg_iterations_per_step"] = float(st["iters"][0]) / w.nsteps
+                else:
+                    num = sum(float(np.sum((a - b) ** 2)) for a, b in zip(ref, p))
+                    den = sum(float(np.sum(a ** 2)) for a in ref)
+                    r["e_h_percent"] = 100.0 * (num / den) ** 0.5
+                res[scheme] = r
+            except Exception as e:  # report, do not abort the benchmark
+                res[scheme] = {"error": str(e)}
+            finally:
+                ctx.close()
+        out["%dC" % L] = res
+    out["workload"] = ("paper_wells: 200x200, 25 seeded fracture segments (k 1e6), p0 = 1, wells "
+                       "q_w = 1e5, p_w = 1.2, tau = 4e-5, 50 steps, FP64, rtol %g; host wall clock "
+                       "per 50-step call" % RTOL_BATCH)
+    return out
+
+
+def batched_extra(args, mc, mi, torch, stream, ws, precond=0):
     """The batched fracture workload (256 instances of 128^2..1024^2, L = 2
     or 3, in the full recipe; the first --batch of them here): one warm-up
     step (graph capture, and instances whose FP32 refinement fails are handed
@@ -248,6 +333,7 @@ def batched_extra(args, mc, mi, torch, stream, ws):
     ob.precision = 1
     ob.rtol = RTOL_BATCH
     ob.ir_max = 12
+    ob.precond = precond  # preconditioner of the FP64 path that takes failed instances
     ctxs = [mc.Context.from_workload(x, opts=ob, stream=stream) for x in wb]
     bt = mc.Batch(ctxs, ob)
     bt.step("D", 1)
@@ -271,6 +357,7 @@ def batched_extra(args, mc, mi, torch, stream, ws):
             "unit": "continuum-cell updates/s", "steps": args.batch_steps, "s_per_step": dt / args.batch_steps,
             "timing": "host wall clock around mc_batch_step (one graph replay + FP64 path for "
                       "handed-over instances), after one warm-up step",
+            "fp64_path_preconditioner": "two-level" if precond else "Jacobi",
             "team": info["team"], "teams": info["teams"],
             "fp64_instances": info["fp64_instances"],
             "inner_iterations_per_step": float(sum(st["iters"])) / args.batch_steps,
@@ -312,11 +399,12 @@ def main():
     L, Ncell = w.L, w.nx * w.ny
     cells_steps = L * Ncell * args.steps
 
-    def opts_for(rtol, precision=0, inner_form=0):
+    def opts_for(rtol, precision=0, inner_form=0, precond=0):
         o = mc.mc_default_opts()
         o.rtol = rtol
         o.precision = precision
         o.inner_form = inner_form
+        o.precond = precond
         return o
 
     def timed_run(scheme, opts):
@@ -363,6 +451,19 @@ def main():
                              "ms_per_step": 1e3 * cdev / args.steps, "rtol": RTOL_COUPLED,
                              "pcg_iterations_per_step": float(np.mean(cits)),
                              "decoupled_speedup": cdev / dev_time}
+        try:
+            tdev, tits, _ = timed_run("D", opts_for(RTOL_D, precond=1))
+            tci = float(sum(tits)) * Ncell
+            extras["fp64_two_level"] = {
+                "value": ws * cells_steps / tdev, "unit": "continuum-cell updates/s",
+                "ms_per_step": 1e3 * tdev / args.steps, "rtol": RTOL_D,
+                "preconditioner": "Jacobi + Galerkin coarse correction on the 64x16 tiles "
+                                  "(1024 coarse unknowns per continuum, dense inverse)",
+                "pcg_iterations_per_step": float(np.mean(tits)),
+                "speedup_vs_jacobi": dev_time / tdev,
+                "speedup_vs_coupled": cdev / tdev}
+        except Exception as e:  # report, do not abort the benchmark
+            extras["fp64_two_level"] = {"error": str(e)}
         for name, prec, form in (("fp32_ir", 1, 0), ("bf16t_ir", 2, 0),
                                  ("fp32_ir_two_reductions", 1, 1)):
             pdev, pits, psw = timed_run("D", opts_for(RTOL_D, prec, form))
@@ -436,8 +537,15 @@ def main():
                           "coarse_steps_per_s": ncs / t_coarse,
                           "coarse_D_e_H_after_5_steps_vs_fine_coupled": e_h}
 
+    if not args.no_extras:
+        extras["precision_4096"] = precision_extra(args, mc, mi, torch, stream, ws, hbm)
+        extras["paper_wells"] = paper_extra(args, mc, mi, np)
     if not args.no_extras and args.batch > 0:
         extras["batched"] = batched_extra(args, mc, mi, torch, stream, ws)
+        try:
+            extras["batched_two_level_fp64"] = batched_extra(args, mc, mi, torch, stream, ws, precond=1)
+        except Exception as e:  # report, do not abort the benchmark
+            extras["batched_two_level_fp64"] = {"error": str(e)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -66,7 +66,14 @@ typedef struct {
 } mc_grid;
 
 enum { MC_PREC_FP64 = 0, MC_PREC_FP32_IR = 1, MC_PREC_BF16T_IR = 2 };
-enum { MC_PRECOND_JACOBI = 0 };
+/* Preconditioners of the FP64 PCG. MC_PRECOND_TWO_LEVEL (decoupled FP64
+   schemes only) adds to Jacobi a Galerkin coarse correction on the 64 x 16
+   stencil tiles, M^-1 = D^-1 + P (P^T A P)^-1 P^T with P the tile
+   indicators; its dense inverse is formed on the device at the first step
+   (at most MC_TWO_LEVEL_MAX_TILES tiles per continuum, else MC_E_ARG). It
+   changes only the Krylov iteration, not the system solved. */
+enum { MC_PRECOND_JACOBI = 0, MC_PRECOND_TWO_LEVEL = 1 };
+#define MC_TWO_LEVEL_MAX_TILES 2048
 /* Inner FP32 PCG of the IR forms: single-reduction (Chronopoulos-Gear)
    recurrences, one grid-wide reduction per iteration, or the textbook
    (Hestenes-Stiefel) recurrences with two. Both are the Jacobi PCG of
@@ -77,7 +84,7 @@ enum { MC_SCHEME_COUPLED = -1, MC_SCHEME_D = 0, MC_SCHEME_L = 1, MC_SCHEME_U = 2
 typedef struct {
   int32_t precision;   /* MC_PREC_*: FP64 PCG, or FP32 / BF16-transmissibility
                           inner PCG inside FP64 iterative refinement */
-  int32_t precond;     /* MC_PRECOND_JACOBI */
+  int32_t precond;     /* MC_PRECOND_JACOBI or MC_PRECOND_TWO_LEVEL */
   int32_t max_iter;    /* PCG iterations per solve (IR forms: cap of each inner
                           solve, further limited to 16 max(nx, ny) within
                           [2048, 16384]; an inner solve also stops when its
@@ -144,6 +151,22 @@ mc_status mc_set_opts(mc_ctx* ctx, const mc_opts* opts);
 /* F_a (cell-integrated source, Eq. app-mc: F = f |cell|), host nx*ny. */
 mc_status mc_set_source(mc_ctx* ctx, int32_t alpha, const double* F);
 
+/*
+ * mc_set_well -- implicit well term of continuum alpha. Section 5 drives its
+ *   experiments by a well source q_w (p - p_w) in the fracture cells of two
+ *   small regions; it is read here as the relaxation q_w (p_w - p) toward the
+ *   well pressure (the dissipative sign) and taken implicitly in p, which
+ *   adds W = q_w |cell| to the diagonal of continuum alpha's own block and
+ *   W p_w to its right-hand side, in every scheme and precision form.
+ *   W   host nx*ny cell-integrated well indices (>= 0, finite; 0 outside the
+ *       wells), or NULL to remove the wells of alpha.
+ *   pw  host nx*ny well pressures (finite); ignored when W is NULL.
+ *   The arrays are copied. Contexts with wells are not accepted by
+ *   mc_nlmc_build (MC_E_STATE); a batch sees the wells its contexts had when
+ *   mc_batch_create ran. MC_E_ARG on a bad alpha or data.
+ */
+mc_status mc_set_well(mc_ctx* ctx, int32_t alpha, const double* W, const double* pw);
+
 /* Copy L host arrays into the state p^n. */
 mc_status mc_set_state(mc_ctx* ctx, const double* const* p);
 
@@ -192,7 +215,7 @@ mc_status mc_apply(mc_ctx* ctx, int32_t scheme, const double* const* x,
                    double* const* y);
 
 /* D-scheme right-hand sides of the current state into L host arrays:
- * b_a = M_a/tau p_a + F_a + sum_b Q_ab p_b. */
+ * b_a = M_a/tau p_a + F_a (+ W_a p_w,a) + sum_b Q_ab p_b. */
 mc_status mc_rhs_decoupled(mc_ctx* ctx, double* const* b);
 
 /* Bytes of device memory the context holds. */
@@ -341,7 +364,7 @@ void mc_batch_destroy(mc_batch* b);
  * This entry point creates no context and calls no cudaMalloc, cudaFree or
  * other allocating routine. All of its scratch (pitched copies of the fields,
  * transmissibilities, PCG vectors, partial sums, barrier words, statistics)
- * lives in one fixed device array of the library, about 5.5 MB, which every
+ * lives in one fixed device array of the library, about 6 MB, which every
  * GPU that loads the library holds until the process exits.
  *
  *   nx, ny    grid; ny * (nx rounded up to 16) must be <= 65536 cells

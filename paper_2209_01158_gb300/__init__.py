@@ -128,6 +128,18 @@ def mc_set_source(ctx, alpha, F, n=None):
     _check(_lib().mc_set_source(ctx, int(alpha), p), ctx)
 
 
+def mc_set_well(ctx, alpha, W, pw, n=None):
+    """Implicit well term of continuum alpha (W = q_w |cell| per cell, p_w per
+    cell); W=None removes it."""
+    if W is None:
+        _check(_lib().mc_set_well(ctx, int(alpha), None, None), ctx)
+        return
+    pw = np.broadcast_to(np.asarray(pw, dtype=np.float64), np.shape(W))
+    w, keep_w = _dptr(np.ascontiguousarray(np.ravel(W), dtype=np.float64), n)
+    q, keep_q = _dptr(np.ascontiguousarray(np.ravel(pw), dtype=np.float64), n)
+    _check(_lib().mc_set_well(ctx, int(alpha), w, q), ctx)
+
+
 def mc_set_state(ctx, p, n=None):
     arr, keep = _dptr_list(p, n)
     _check(_lib().mc_set_state(ctx, arr), ctx)
@@ -310,6 +322,8 @@ class Context:
                   w.tau, opts, stream)
         for a in range(w.L):
             ctx.set_source(a, w.F[a])
+        for a, (W, pw) in (getattr(w, "wells", None) or {}).items():
+            ctx.set_well(a, W, pw)
         ctx.set_state(w.p0)
         return ctx
 
@@ -322,6 +336,9 @@ class Context:
 
     def set_source(self, alpha, F):
         mc_set_source(self._ctx, alpha, np.ravel(F) if not hasattr(F, "data_ptr") else F, self.n)
+
+    def set_well(self, alpha, W, pw):
+        mc_set_well(self._ctx, alpha, W, pw, self.n)
 
     def set_state(self, p):
         mc_set_state(self._ctx, [np.ravel(x) if not hasattr(x, "data_ptr") else x for x in p],

@@ -13,7 +13,8 @@ LIB_PATH = os.path.join(_HERE, "libmc.so")
 MC_MAX_CONTINUA = 4
 MC_OK, MC_E_ARG, MC_E_ALLOC, MC_E_CUDA, MC_E_NOCONV, MC_E_TIMEOUT, MC_E_STATE, MC_E_BREAKDOWN = range(8)
 MC_PREC_FP64, MC_PREC_FP32_IR, MC_PREC_BF16T_IR = 0, 1, 2
-MC_PRECOND_JACOBI = 0
+MC_PRECOND_JACOBI, MC_PRECOND_TWO_LEVEL = 0, 1
+MC_TWO_LEVEL_MAX_TILES = 2048
 MC_INNER_SINGLE_REDUCTION, MC_INNER_TWO_REDUCTIONS = 0, 1
 MC_SCHEME_COUPLED, MC_SCHEME_D, MC_SCHEME_L, MC_SCHEME_U = -1, 0, 1, 2
 
@@ -50,6 +51,7 @@ SIGNATURES = {
                            C.POINTER(mc_opts), C.c_void_p, C.POINTER(C.c_void_p)]),
     "mc_set_opts": (C.c_int, [C.c_void_p, C.POINTER(mc_opts)]),
     "mc_set_source": (C.c_int, [C.c_void_p, C.c_int32, dp]),
+    "mc_set_well": (C.c_int, [C.c_void_p, C.c_int32, dp, dp]),
     "mc_set_state": (C.c_int, [C.c_void_p, dpp]),
     "mc_get_state": (C.c_int, [C.c_void_p, dpp]),
     "mc_state_device": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),

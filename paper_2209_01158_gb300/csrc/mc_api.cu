@@ -76,7 +76,10 @@ int launch_blocks(const mc_ctx* ctx) {
 
 mc_status check_opts(const mc_opts* o, std::string* why) {
   if (o->precision < MC_PREC_FP64 || o->precision > MC_PREC_BF16T_IR) { *why = "precision"; return MC_E_ARG; }
-  if (o->precond != MC_PRECOND_JACOBI) { *why = "precond"; return MC_E_ARG; }
+  if (o->precond != MC_PRECOND_JACOBI && o->precond != MC_PRECOND_TWO_LEVEL) {
+    *why = "precond";
+    return MC_E_ARG;
+  }
   if (o->max_iter < 1) { *why = "max_iter < 1"; return MC_E_ARG; }
   if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) { *why = "rtol must be in (0, 1)"; return MC_E_ARG; }
   if (o->spin_limit < 1) { *why = "spin_limit < 1"; return MC_E_ARG; }
@@ -144,9 +147,12 @@ void mc_fill_params(const mc_ctx* ctx, StepParams* sp, int scheme, int nsteps) {
     sp->TN[a] = ctx->TN[a];
     sp->invd[a] = ctx->invd[a];
     sp->F[a] = ctx->F[a];
+    sp->W[a] = ctx->W[a];
+    sp->FW[a] = ctx->FW[a];
     sp->p[a] = ctx->p[a];
     sp->pprev[a] = ctx->pprev[a];
     sp->r[a] = ctx->r[a];
+    sp->z[a] = ctx->z[a];
     sp->P[0][a] = ctx->P[0][a];
     sp->P[1][a] = ctx->P[1][a];
     sp->q[a] = ctx->q[a];
@@ -295,6 +301,7 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
     CKS(mc_alloc(ctx, (void**)&ctx->p[a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->pprev[a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->r[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->z[a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->P[0][a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->P[1][a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->q[a], fb));
@@ -324,6 +331,8 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
   // TMA descriptors of the tiles the stencil phase stages in shared memory.
   for (int a = 0; a < L; ++a) {
     const int bx = mc_step_box_x(), by = mc_step_box_y();
+    CKS(mc_encode_map(&ctx->maps.z[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, ctx->z[a], ctx->nx, ctx->ny,
+                      ctx->pitch, bx, by));
     CKS(mc_encode_map(&ctx->maps.r[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, ctx->r[a], ctx->nx, ctx->ny,
                       ctx->pitch, bx, by));
     CKS(mc_encode_map(&ctx->maps.P[0][a], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, ctx->P[0][a], ctx->nx,
@@ -366,6 +375,39 @@ mc_status mc_set_source(mc_ctx* ctx, int32_t alpha, const double* F) {
   return MC_OK;
 }
 
+mc_status mc_set_well(mc_ctx* ctx, int32_t alpha, const double* W, const double* pw) {
+  if (!ctx) return MC_E_ARG;
+  if (alpha < 0 || alpha >= ctx->L) return set_err(ctx, MC_E_ARG, "bad alpha");
+  if (W) {
+    if (!pw) return set_err(ctx, MC_E_ARG, "pw is NULL");
+    for (long long i = 0; i < ctx->N; ++i) {
+      if (!isfinite(W[i]) || W[i] < 0.0) return set_err(ctx, MC_E_ARG, "W must be finite and >= 0");
+      if (!isfinite(pw[i])) return set_err(ctx, MC_E_ARG, "pw must be finite");
+    }
+  }
+  CK(cudaSetDevice(ctx->device));
+  const size_t fb = (size_t)ctx->Np * sizeof(double);
+  if (W) {
+    if (!ctx->W[alpha]) {
+      CK(mc_alloc(ctx, (void**)&ctx->W[alpha], fb));
+      CK(mc_alloc(ctx, (void**)&ctx->FW[alpha], fb));
+    }
+    // the well makes diag(A0 - D) vary per cell
+    if (!ctx->diagc[alpha]) CK(mc_alloc(ctx, (void**)&ctx->diagc[alpha], fb));
+    CK(h2d(ctx, ctx->W[alpha], W));
+    CK(h2d(ctx, ctx->FW[alpha], pw));
+    CK(mc_launch_well(ctx, alpha));
+  } else {
+    ctx->W[alpha] = nullptr;  // the buffers stay allocated until mc_destroy
+    ctx->FW[alpha] = nullptr;
+  }
+  CK(mc_launch_diag(ctx, alpha));
+  ctx->lo_kind = 0;  // FP32 / BF16 copies of diag and invd are stale
+  ctx->tl_ready = 0;  // so is the two-level coarse operator
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MC_OK;
+}
+
 mc_status mc_set_state(mc_ctx* ctx, const double* const* p) {
   if (!ctx) return MC_E_ARG;
   if (!p) return set_err(ctx, MC_E_ARG, "p is NULL");
@@ -394,16 +436,64 @@ mc_status mc_state_device(mc_ctx* ctx, int32_t alpha, double** dev) {
   return MC_OK;
 }
 
+// Two-level preconditioner set-up: the coarse operator of every continuum on
+// the stencil tiles and its dense inverse (Gauss-Jordan on the device), once
+// per context and again after the diagonal changes (mc_set_well).
+static mc_status tl_prepare(mc_ctx* ctx) {
+  if (ctx->tl_ready) return MC_OK;
+  const int nc = mc_step_tiles(ctx->nx, ctx->ny);
+  if (nc > MC_TWO_LEVEL_MAX_TILES)
+    return set_err(ctx, MC_E_ARG, "two-level preconditioner: more than MC_TWO_LEVEL_MAX_TILES tiles");
+  if (!ctx->tl_work) {
+    CK(mc_alloc(ctx, (void**)&ctx->tl_work, 2 * (size_t)nc * sizeof(double)));
+    CK(mc_alloc(ctx, (void**)&ctx->tl_bar, 96 * sizeof(unsigned)));
+    for (int a = 0; a < ctx->L; ++a) {
+      CK(mc_alloc(ctx, (void**)&ctx->tl_Ainv[a], (size_t)nc * nc * sizeof(double)));
+      CK(mc_alloc(ctx, (void**)&ctx->tl_g[a], (size_t)nc * sizeof(double)));
+      CK(mc_alloc(ctx, (void**)&ctx->tl_c[a], (size_t)nc * sizeof(double)));
+    }
+    ctx->tl_nc = nc;
+  }
+  CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), ctx->stream));
+  for (int a = 0; a < ctx->L; ++a) {
+    CK(mc_launch_coarse_assemble(ctx, a, ctx->tl_Ainv[a]));
+    CK(mc_gj_invert(ctx->tl_Ainv[a], nc, ctx->tl_work, ctx->tl_bar, ctx->dstatus, ctx->opts.spin_limit,
+                    ctx->num_sms, ctx->stream));
+  }
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st != MC_OK) return set_err(ctx, (mc_status)st, "two-level preconditioner set-up");
+  ctx->tl_ready = 1;
+  return MC_OK;
+}
+
 static mc_status run_steps(mc_ctx* ctx, int scheme, int nsteps, mc_stats* stats) {
   if (stats) memset(stats, 0, sizeof(*stats));
   if (nsteps < 0) return set_err(ctx, MC_E_ARG, "nsteps < 0");
   const bool ir = ctx->opts.precision != MC_PREC_FP64;
   if (ir && scheme == MC_SCHEME_COUPLED)
     return set_err(ctx, MC_E_ARG, "the precision form applies to the decoupled schemes");
+  const bool tl = ctx->opts.precond == MC_PRECOND_TWO_LEVEL;
+  if (tl && (ir || scheme == MC_SCHEME_COUPLED))
+    return set_err(ctx, MC_E_ARG, "the two-level preconditioner applies to the FP64 decoupled schemes");
   if (nsteps == 0) return MC_OK;
   CK(cudaSetDevice(ctx->device));
+  if (tl) {
+    const mc_status ps = tl_prepare(ctx);
+    if (ps != MC_OK) return ps;
+  }
   StepParams sp;
   mc_fill_params(ctx, &sp, scheme, nsteps);
+  if (tl) {
+    sp.two_level = 1;
+    sp.nc = ctx->tl_nc;
+    for (int a = 0; a < ctx->L; ++a) {
+      sp.Ainv[a] = ctx->tl_Ainv[a];
+      sp.gsum[a] = ctx->tl_g[a];
+      sp.ccor[a] = ctx->tl_c[a];
+    }
+  }
   CK(cudaMemsetAsync(ctx->bar, 0, 96 * sizeof(unsigned), ctx->stream));
   CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(ctx->dsteps, 0, sizeof(int), ctx->stream));

@@ -225,6 +225,7 @@ mc_status fp64_steps(mc_batch* b, int i, int scheme, int nsteps) {
   mc_ctx* c = b->ctx[i];
   const mc_opts save = c->opts;
   c->opts.precision = MC_PREC_FP64;
+  c->opts.precond = b->opts.precond;
   c->opts.rtol = b->opts.rtol;
   c->opts.max_iter = b->opts.max_iter;
   c->opts.spin_limit = b->opts.spin_limit;
@@ -357,7 +358,8 @@ mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t n, const mc_opts* opts, m
     return berr(nullptr, MC_E_ARG, "the batched form needs precision MC_PREC_FP32_IR or MC_PREC_BF16T_IR");
   if (opts->max_iter < 1 || !(opts->rtol > 0.0) || !(opts->rtol < 1.0) || opts->spin_limit < 1 ||
       opts->blocks < 0 || opts->ir_max < 0 || !(opts->inner_rtol > 0.0) || !(opts->inner_rtol < 1.0) ||
-      (opts->inner_form != MC_INNER_SINGLE_REDUCTION && opts->inner_form != MC_INNER_TWO_REDUCTIONS))
+      (opts->inner_form != MC_INNER_SINGLE_REDUCTION && opts->inner_form != MC_INNER_TWO_REDUCTIONS) ||
+      (opts->precond != MC_PRECOND_JACOBI && opts->precond != MC_PRECOND_TWO_LEVEL))
     return berr(nullptr, MC_E_ARG, "opts out of range");
   for (int i = 0; i < n; ++i)
     if (!ctxs[i]) return berr(nullptr, MC_E_ARG, "context " + std::to_string(i) + " is NULL");

@@ -37,9 +37,12 @@ struct StepParams {
   const double* TN[MCL];
   const double* invd[MCL];
   const double* F[MCL];
+  const double* W[MCL];            // well index q_w |cell| per cell, or nullptr
+  const double* FW[MCL];           // W p_w per cell, or nullptr
   double* p[MCL];
   double* pprev[MCL];
   double* r[MCL];
+  double* z[MCL];                  // M r, written by the pointwise phase
   double* P[2][MCL];
   double* q[MCL];
   double* partials;                // [2 slots][4 quantities][MCL][nblocks]
@@ -52,6 +55,12 @@ struct StepParams {
   double* relres;                  // [MCL]
   double* mass_defect;             // [1]
   long long spin_limit;
+  // two-level preconditioner (decoupled FP64 path; two_level = 0: Jacobi)
+  int two_level;
+  int nc;                          // coarse unknowns per continuum (stencil tiles)
+  const double* Ainv[MCL];         // nc x nc inverse of the coarse operator
+  double* gsum[MCL];               // P^T r (tile sums)
+  double* ccor[MCL];               // coarse correction A_c^-1 P^T r
 };
 
 // TMA descriptors of the arrays the stencil phase reads through tiles.
@@ -63,6 +72,7 @@ struct TmaMaps {
   CUtensorMap invd[MCL];
   CUtensorMap q[MCL];
   CUtensorMap w[2][MCL];
+  CUtensorMap z[MCL];            // FP64 step kernel: z = M r
 };
 
 // Extra state of the precision form (FP32 inner PCG in FP64 refinement).
@@ -139,13 +149,24 @@ struct mc_ctx {
   double* diagc[MCL] = {};
   double* qcell[MCL][MCL] = {};
   double* F[MCL] = {};
+  double* W[MCL] = {};             // wells (mc_set_well), nullptr when none
+  double* FW[MCL] = {};
   double* p[MCL] = {};
   double* pprev[MCL] = {};
   double* r[MCL] = {};
+  double* z[MCL] = {};
   double* P[2][MCL] = {};
   double* q[MCL] = {};
   double* partials = nullptr;
   size_t partials_len = 0;
+  // two-level preconditioner (allocated and factorised on first use)
+  double* tl_Ainv[MCL] = {};
+  double* tl_g[MCL] = {};
+  double* tl_c[MCL] = {};
+  double* tl_work = nullptr;
+  unsigned* tl_bar = nullptr;
+  int tl_nc = 0;
+  int tl_ready = 0;
   int maxb = 0;                    // CTAs the partials buffer is sized for
   // precision form (allocated on first use)
   float* r32[MCL] = {};
@@ -185,6 +206,17 @@ cudaError_t mc_launch_steps(mc_ctx* ctx, const StepParams& sp, int blocks,
 cudaError_t mc_launch_steps_raw(const StepParams& sp, const TmaMaps& maps, int blocks,
                                 int threads, cudaStream_t stream);
 
+// In-place Gauss-Jordan inverse of an n x n SPD matrix on the device (one
+// cooperative launch; work holds 2n doubles, bar 96 zeroed words of its own).
+cudaError_t mc_gj_invert(double* M, int n, double* work, unsigned* bar, int* status,
+                         long long spin_limit, int num_sms, cudaStream_t stream);
+
+// Two-level preconditioner (mc_step.cu): coarse operator A_c = P^T (M/tau + A0) P
+// of continuum a on the 64 x 16 stencil tiles (P = tile indicators), dense
+// nc x nc, assembled into Ac (overwritten).
+cudaError_t mc_launch_coarse_assemble(const mc_ctx* ctx, int a, double* Ac);
+int mc_step_tiles(int nx, int ny);
+
 // Maximum co-resident CTAs for the step kernel of this L (cooperative grid).
 int mc_step_max_blocks(int L, int threads, int num_sms);
 int mc_step_box_x();
@@ -217,6 +249,8 @@ cudaError_t mc_launch_single_setup(int nx, int ny, int pitch, double h, double c
                                    const double* k, double* TE, double* TN, double* invd,
                                    cudaStream_t stream);
 cudaError_t mc_launch_diag(mc_ctx* ctx, int a);
+// FW = W * pw in place (FW holds pw on entry), pitched arrays.
+cudaError_t mc_launch_well(mc_ctx* ctx, int a);
 cudaError_t mc_launch_apply(mc_ctx* ctx, int scheme, double* const* x,
                             double* const* y);
 cudaError_t mc_launch_rhs(mc_ctx* ctx, double* const* b);

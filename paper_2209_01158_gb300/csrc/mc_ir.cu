@@ -442,6 +442,11 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
         const double f = __ldg(sp.F[a] + i);
         double rv = f + sp.mtau[a] * (xp - xc);
         double bv = sp.mtau[a] * xp + f;
+        if (sp.W[a]) {  // implicit well term: b += W p_w, A x += W x
+          const double fw = __ldg(sp.FW[a] + i);
+          rv += fw - __ldg(sp.W[a] + i) * xc;
+          bv += fw;
+        }
 #pragma unroll
         for (int b = 0; b < L; ++b) {
           if (b == a) continue;
@@ -1054,8 +1059,9 @@ cudaError_t mc_ir_prepare(mc_ctx* ctx, int bf16) {
         if ((e = mc_alloc(ctx, (void**)&ctx->invd32[a], fb4)) != cudaSuccess) return e;
         if ((e = mc_alloc(ctx, (void**)&ctx->TElo32[a], fb4)) != cudaSuccess) return e;
         if ((e = mc_alloc(ctx, (void**)&ctx->TNlo32[a], fb4)) != cudaSuccess) return e;
-        if (ctx->diagc[a] && (e = mc_alloc(ctx, (void**)&ctx->dc32[a], fb4)) != cudaSuccess) return e;
       }
+      if (ctx->diagc[a] && !ctx->dc32[a] && (e = mc_alloc(ctx, (void**)&ctx->dc32[a], fb4)) != cudaSuccess)
+        return e;
       // bf16 copies live in the first half of the FP32 buffers
       lo_copy_kernel<<<1024, 256, 0, ctx->stream>>>(ctx->Np, ctx->TE[a], ctx->TN[a], ctx->invd[a],
                                                     ctx->diagc[a], ctx->TElo32[a], ctx->TNlo32[a],

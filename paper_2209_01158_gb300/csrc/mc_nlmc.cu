@@ -704,6 +704,25 @@ __global__ void copy_full_kernel(const double* Abar, long long n, const double* 
 
 }  // namespace
 
+cudaError_t mc_gj_invert(double* M, int n, double* work, unsigned* bar, int* status,
+                         long long spin_limit, int num_sms, cudaStream_t stream) {
+  GJArgs g{};
+  g.bar.count = reinterpret_cast<unsigned long long*>(bar);
+  g.bar.abort_word = bar + 64;
+  g.bar.status = status;
+  g.bar.spin_limit = spin_limit;
+  g.M = M;
+  g.row = work;
+  g.col = work + n;
+  g.n = n;
+  cudaError_t e = cudaMemsetAsync(bar, 0, 96 * sizeof(unsigned), stream);
+  if (e != cudaSuccess) return e;
+  const int blocks = coop_blocks((void*)gj_invert_kernel, 512, num_sms);
+  if (blocks < 1) return cudaErrorInvalidConfiguration;
+  void* args[] = {&g};
+  return cudaLaunchCooperativeKernel((void*)gj_invert_kernel, dim3(blocks), dim3(512), args, 0, stream);
+}
+
 extern "C" {
 
 mc_status mc_nlmc_build(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
@@ -716,6 +735,11 @@ mc_status mc_nlmc_build(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
     return MC_E_ARG;
   }
   if (!(basis_rtol > 0.0) || !(basis_rtol < 1.0) || basis_max_iter < 1) return MC_E_ARG;
+  for (int a = 0; a < ctx->L; ++a)
+    if (ctx->W[a]) {
+      ctx->err = "the coarse model takes no wells (mc_set_well)";
+      return MC_E_STATE;
+    }
   const int bx = ctx->nx / ncx, by = ctx->ny / ncy;
   const int span = 2 * layers + 1;
   if ((span < ncx ? span : ncx) * (span < ncy ? span : ncy) * ctx->L > MAXBLK) {

@@ -6,7 +6,7 @@
 // the PCG vectors, the per-CTA partial sums, the grid-barrier words and the
 // run statistics -- lives in ONE file-scope device array of fixed size. The
 // array belongs to the loaded module, so every GPU that loads this library
-// holds it (about 5.5 MB) until the process exits.
+// holds it (about 6 MB) until the process exits.
 //
 // In host code the array's name is only a host-side stand-in for the device
 // symbol. Its device address is looked up once per device with
@@ -23,7 +23,7 @@
 namespace {
 
 constexpr long long kMaxCells = 65536;   // ny * pitch, pitch = nx rounded up to 16
-constexpr int kFields = 10;              // k/r, TE, TN, invd, F, p, pprev, P0, P1, q
+constexpr int kFields = 11;              // k/r, TE, TN, invd, F, p, pprev, P0, P1, q, z
 constexpr int kMaxBlocks = 1024;
 constexpr long long kPartials = 2LL * 4 * MCL * kMaxBlocks;
 constexpr long long kCtrl = 256;         // barrier words, status, statistics
@@ -77,7 +77,7 @@ extern "C" mc_status mc_step_single_noalloc(int32_t nx, int32_t ny, const double
   for (int f = 0; f < kFields; ++f) fld[f] = base + f * kMaxCells;
   double* kk = fld[0];  // holds k during set-up, then serves as r
   double *TE = fld[1], *TN = fld[2], *invd = fld[3], *Fp = fld[4], *pp = fld[5], *pprev = fld[6];
-  double *P0 = fld[7], *P1 = fld[8], *q = fld[9];
+  double *P0 = fld[7], *P1 = fld[8], *q = fld[9], *zb = fld[10];
   double* partials = base + kFields * kMaxCells;
   double* ctrl = partials + kPartials;
   unsigned* bar = reinterpret_cast<unsigned*>(ctrl);               // 96 words
@@ -105,7 +105,7 @@ extern "C" mc_status mc_step_single_noalloc(int32_t nx, int32_t ny, const double
   TmaMaps maps;
   memset(&maps, 0, sizeof(maps));
   const int bx = mc_step_box_x(), by = mc_step_box_y();
-  NA_CK(mc_encode_map(&maps.r[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, kk, nx, ny, pitch, bx, by));
+  NA_CK(mc_encode_map(&maps.z[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, zb, nx, ny, pitch, bx, by));
   NA_CK(mc_encode_map(&maps.P[0][0], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, P0, nx, ny, pitch, bx, by));
   NA_CK(mc_encode_map(&maps.P[1][0], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, P1, nx, ny, pitch, bx, by));
   NA_CK(mc_encode_map(&maps.invd[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, invd, nx, ny, pitch, bx, by));
@@ -133,6 +133,7 @@ extern "C" mc_status mc_step_single_noalloc(int32_t nx, int32_t ny, const double
   sp.p[0] = pp;
   sp.pprev[0] = pprev;
   sp.r[0] = kk;
+  sp.z[0] = zb;
   sp.P[0][0] = P0;
   sp.P[1][0] = P1;
   sp.q[0] = q;

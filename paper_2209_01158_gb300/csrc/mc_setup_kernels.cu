@@ -51,6 +51,7 @@ struct DiagArgs {
   const double* qcell[MCL];
   const double* TE;
   const double* TN;
+  const double* W;  // well index per cell, or nullptr
   double* diagc;  // may be nullptr (constant case)
   double* invd;
 };
@@ -66,6 +67,7 @@ __global__ void diag_kernel(DiagArgs g) {
       if (b == g.a) continue;
       dc += g.qcell[b] ? g.qcell[b][i] : g.qconst[b];
     }
+    if (g.W) dc += g.W[i];
     double t = g.TE[i] + g.TN[i];
     if (gx > 0) t += g.TE[i - 1];
     if (gy > 0) t += g.TN[i - g.pitch];
@@ -85,7 +87,9 @@ struct ApplyArgs {
   const double* x[MCL];
   double* y[MCL];
   const double* F[MCL];
-  bool rhs;  // y_a = mtau x_a + F_a + sum_b q_ab x_b instead of the operator
+  const double* W[MCL];   // wells, or nullptr
+  const double* FW[MCL];
+  bool rhs;  // y_a = mtau x_a + F_a (+ W_a pw_a) + sum_b q_ab x_b instead of the operator
 };
 
 __device__ __forceinline__ double q_of(const ApplyArgs& g, int a, int b, long long i) {
@@ -104,10 +108,12 @@ __global__ void apply_kernel(ApplyArgs g) {
       double v;
       if (g.rhs) {
         v = g.mtau[a] * xc + g.F[a][i];
+        if (g.FW[a]) v += g.FW[a][i];
         for (int b = 0; b < g.L; ++b)
           if (b != a) v += q_of(g, a, b, i) * g.x[b][i];
       } else {
         v = g.mtau[a] * xc;
+        if (g.W[a]) v += g.W[a][i] * xc;
         if (gx + 1 < nx) v += g.TE[a][i] * (xc - g.x[a][i + 1]);
         if (gx > 0) v += g.TE[a][i - 1] * (xc - g.x[a][i - 1]);
         if (gy + 1 < g.ny) v += g.TN[a][i] * (xc - g.x[a][i + pitch]);
@@ -165,9 +171,21 @@ cudaError_t mc_launch_diag(mc_ctx* ctx, int a) {
   }
   g.TE = ctx->TE[a];
   g.TN = ctx->TN[a];
+  g.W = ctx->W[a];
   g.diagc = ctx->diagc[a];
   g.invd = ctx->invd[a];
   diag_kernel<<<grid_for(ctx->Np), 256, 0, ctx->stream>>>(g);
+  return cudaGetLastError();
+}
+
+__global__ void well_kernel(long long Np, const double* __restrict__ W, double* __restrict__ FW) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Np;
+       i += (long long)gridDim.x * blockDim.x)
+    FW[i] = W[i] * FW[i];
+}
+
+cudaError_t mc_launch_well(mc_ctx* ctx, int a) {
+  well_kernel<<<grid_for(ctx->Np), 256, 0, ctx->stream>>>(ctx->Np, ctx->W[a], ctx->FW[a]);
   return cudaGetLastError();
 }
 
@@ -181,6 +199,8 @@ static void fill_apply(const mc_ctx* ctx, ApplyArgs* g) {
     g->TE[a] = ctx->TE[a];
     g->TN[a] = ctx->TN[a];
     g->F[a] = ctx->F[a];
+    g->W[a] = ctx->W[a];
+    g->FW[a] = ctx->FW[a];
     for (int b = 0; b < ctx->L; ++b) {
       g->qconst[a][b] = ctx->sigma[a][b] * ctx->h * ctx->h;
       g->qcell[a][b] = ctx->qcell[a][b];

@@ -14,12 +14,12 @@
 // row). The PCG warm-starts from p^{n-1} and updates p in place.
 //
 // PCG iteration = two phases separated by grid barriers:
-//   A (stencil): per 64 x 16 tile, TMA brings the halo boxes of r, P_old and
-//     invd into shared memory (a ring of up to 6 stages: the next tiles'
-//     boxes load while this one computes); P_new = invd*r + beta*P_old on the 66 x 18
-//     halo region, then q = A P_new on the tile and <P_new, q>.
-//   B (pointwise, vectorised): x += alpha P_new, r -= alpha q, <r, r>,
-//     <r, invd r>.
+//   A (stencil): per 64 x 16 tile, TMA brings the halo boxes of z = M r and
+//     P_old into shared memory (a ring of up to 8 stages: the next tiles'
+//     boxes load while this one computes); P_new = z + beta*P_old on the
+//     66 x 18 halo region, then q = A P_new on the tile and <P_new, q>.
+//   B (pointwise, vectorised): x += alpha P_new, r -= alpha q, z = invd r
+//     (stored for the next phase A), <r, r>, <r, z>.
 // Cross-CTA data written inside the launch is read through L2 (ld.cg or TMA,
 // after a proxy fence); read-only coefficients use the read-only path.
 // Reductions are deterministic: warp butterflies, then fixed-order sums over
@@ -50,7 +50,7 @@ constexpr int KMAX = 4 * MCL;   // partial-sum quantities per slot
 // TMA pipeline depth: enough boxes in flight per SM to cover the DRAM
 // latency (Little's law: ~64 KB per SM), within 227 KB of shared memory.
 __host__ __device__ constexpr int nstage(int L, bool coupled) {
-  return !coupled ? 6 : (L <= 1 ? 6 : (L == 2 ? 3 : (L == 3 ? 2 : 1)));
+  return !coupled ? 8 : (L <= 1 ? 8 : (L == 2 ? 4 : (L == 3 ? 3 : 2)));
 }
 
 __device__ __forceinline__ double ldc(const double* p) { return __ldcg(p); }
@@ -148,6 +148,7 @@ __device__ __forceinline__ double stencil_flux(const StepParams& sp, int a, cons
 // FP64 divisions and convergence tests run once per CTA, not per thread.
 struct Scal64 {
   double bb[MCL], rr[MCL], rz[MCL], beta[MCL], alpha[MCL];
+  double rzl[MCL];  // two-level: (r, D^-1 r) before the coarse term is added
   int iters[MCL];
   unsigned active;
   int flag;  // 1 breakdown
@@ -160,7 +161,83 @@ struct Smem {
   double* red;      // [NT/32][KMAX]
   double* res;      // [KMAX]
   uint64_t* bar;    // [NST]
+  double* cn;       // [9] coarse corrections of a tile and its neighbours
 };
+
+// ---------------------------------------------------------------------------
+// Two-level preconditioner (an option beside Jacobi):
+//   M^-1 r = D^-1 r + P A_c^-1 P^T r,  A_c = P^T A P,
+// where P holds the indicator vectors of the 64 x 16 stencil tiles and A is
+// the continuum's own system matrix M_a/tau + D_a + sum_b Q_ab (+ W_a). A_c is
+// the Galerkin coarse operator (5-point on the tile grid); its dense inverse
+// is formed once at set-up. Both terms are symmetric positive (semi)definite,
+// so M^-1 is SPD and the CG recurrences are unchanged. The coarse space holds
+// the constant vector, the near-null mode of the zero-flux systems.
+
+// P^T r: the sum of r over every tile of the continua in `act`, tiles handed
+// out to the CTAs as in the stencil phase (deterministic sums).
+template <int L>
+__device__ void tile_rsums(const StepParams& sp, unsigned act, Smem& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int alist[L];
+  int nact = 0;
+#pragma unroll
+  for (int a = 0; a < L; ++a) if (act & (1u << a)) alist[nact++] = a;
+  const int tiles = sp.tiles_x * sp.tiles_y;
+  const int lx = tid % TX, ly = tid / TX;
+  for (int t = blockIdx.x; t < nact * tiles; t += gridDim.x) {
+    const int w = t / tiles, tt = t - w * tiles;
+    int a0 = 0;
+#pragma unroll
+    for (int k = 0; k < L; ++k) if (k == w) a0 = alist[k];
+    const int gx = (tt % sp.tiles_x) * TX + lx, y0 = (tt / sp.tiles_x) * TY;
+    double v = 0.0;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      const int gy = y0 + ly + RPT * j;
+      if (gx < sp.nx && gy < sp.ny) v += ldc(sp.r[a0] + (long long)gy * sp.pitch + gx);
+    }
+    v = warp_sum(v);
+    if (lane == 0) sm.red[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double g = 0.0;
+      for (int k = 0; k < NT / 32; ++k) g += sm.red[k];
+      sp.gsum[a0][tt] = g;
+    }
+    __syncthreads();
+  }
+}
+
+// c_a = A_c^-1 (P^T r)_a for the continua in `act`, one warp per row, and
+// this CTA's share of (P^T r_a) . c_a in gc (lane 0 of each warp).
+template <int L>
+__device__ void coarse_correct(const StepParams& sp, unsigned act, Smem& sm, double (&gc)[L]) {
+  const int nc = sp.nc;
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * NT + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * NT) >> 5;
+  double* sg = sm.box;  // P^T r staged in the idle TMA ring
+#pragma unroll
+  for (int a = 0; a < L; ++a) {
+    gc[a] = 0.0;
+    if (!(act & (1u << a))) continue;
+    for (int J = threadIdx.x; J < nc; J += NT) sg[J] = ldc(sp.gsum[a] + J);
+    __syncthreads();
+    const double* Ai = sp.Ainv[a];
+    for (long long I = gw; I < nc; I += nw) {
+      const double* row = Ai + I * nc;
+      double v = 0.0;
+      for (int J = lane; J < nc; J += 32) v = fma(ldr(row + J), sg[J], v);
+      v = warp_sum(v);
+      if (lane == 0) {
+        sp.ccor[a][I] = v;
+        gc[a] = fma(sg[I], v, gc[a]);
+      }
+    }
+    __syncthreads();
+  }
+}
 
 // ---------------------------------------------------------------------------
 // One linear solve: the continua in `mask` (decoupled, independent systems),
@@ -170,7 +247,7 @@ template <int L, bool COUPLED>
 __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned mask, Smem& sm,
                           uint32_t& phb) {
   constexpr int NL = COUPLED ? L : 1;
-  constexpr int NARR = 3 * NL;
+  constexpr int NARR = 2 * NL;
   constexpr int NST = nstage(L, COUPLED);
   const int nx = sp.nx, ny = sp.ny, pitch = sp.pitch;
   const long long Np = sp.Np;
@@ -190,7 +267,12 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
       if (gx >= nx) continue;
       const double xc = ldc(pa + i);
-      const double f = ldr(sp.F[a] + i);
+      double f = ldr(sp.F[a] + i);
+      double wx = 0.0;  // implicit well term: b += W p_w, A x += W x
+      if (sp.W[a]) {
+        f += ldr(sp.FW[a] + i);
+        wx = ldr(sp.W[a] + i) * xc;
+      }
       double ex = 0.0, exb = 0.0;
 #pragma unroll
       for (int b = 0; b < L; ++b) {
@@ -200,11 +282,12 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
         ex += qv * (pb - xc);
         exb += qv * pb;
       }
-      const double rv = f + ex - stencil_flux(sp, a, pa, gx, gy, i, xc);
+      const double rv = (f - wx) + ex - stencil_flux(sp, a, pa, gx, gy, i, xc);
       const double bv = COUPLED ? sp.mtau[a] * xc + f : sp.mtau[a] * xc + f + exb;
       const double z = ldr(sp.invd[a] + i) * rv;
       sp.r[a][i] = rv;
-      sp.P[0][a][i] = z;
+      sp.z[a][i] = z;
+      sp.P[0][a][i] = z;  // P_old of the first iteration (beta = 0): any finite value
       acc[0 * L + a] += bv * bv;
       acc[1 * L + a] += rv * rv;
       acc[2 * L + a] += rv * z;
@@ -240,6 +323,22 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
   int cur = 0;
   int slot = 1;
   bool ok = true;
+  const bool TL = !COUPLED && sp.two_level;
+  if (TL && active) {
+    // z_0 = D^-1 r_0 + P c_0: the coarse term, and its share of (r_0, z_0)
+    tile_rsums<L>(sp, active, sm);
+    if (!grid_sync(sp)) return false;
+    double gc[L];
+    coarse_correct<L>(sp, active, sm, gc);
+    block_store<L>(gc, active, sm.box, sp.partials, slot);
+    if (!grid_sync(sp)) return false;
+    grid_totals<L>(sp.partials, slot, sm.res);
+    slot ^= 1;
+    if (tid == 0)
+      for (int a = 0; a < L; ++a)
+        if (active & (1u << a)) S.rz[a] += sm.res[a];
+    __syncthreads();
+  }
 
   const int tiles = sp.tiles_x * sp.tiles_y;
   const int lx = tid % TX, ly = tid / TX;  // own cells (lx, ly + RPT * j), j < CPT
@@ -277,9 +376,8 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
 #pragma unroll
       for (int l = 0; l < NL; ++l) {
         const int a = COUPLED ? l : a0;
-        tma_load_2d(base + (3 * l + 0) * ABOX, &maps.r[a], bx0, by0, bar);
-        tma_load_2d(base + (3 * l + 1) * ABOX, &maps.P[cur][a], bx0, by0, bar);
-        tma_load_2d(base + (3 * l + 2) * ABOX, &maps.invd[a], bx0, by0, bar);
+        tma_load_2d(base + (2 * l + 0) * ABOX, &maps.z[a], bx0, by0, bar);
+        tma_load_2d(base + (2 * l + 1) * ABOX, &maps.P[cur][a], bx0, by0, bar);
       }
     };
 
@@ -343,20 +441,31 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       }
       phb ^= 1u << s;
       pend &= ~(1u << s);
+      if (TL) {
+        // c of this tile and of its 8 neighbours (0 outside the tile grid)
+        if (tid < 9) {
+          const int cx = tt % sp.tiles_x + tid % 3 - 1, cy = tt / sp.tiles_x + tid / 3 - 1;
+          sm.cn[tid] = (cx >= 0 && cx < sp.tiles_x && cy >= 0 && cy < sp.tiles_y)
+                           ? ldc(sp.ccor[a0] + cy * sp.tiles_x + cx)
+                           : 0.0;
+        }
+        __syncthreads();
+      }
       const double* base = sm.box + (size_t)s * NARR * ABOX;
       // P_new on the 66 x 18 halo region (box columns 1..66)
 #pragma unroll
       for (int l = 0; l < NL; ++l) {
         const int a = COUPLED ? l : a0;
         const double bt = S.beta[a];
-        const double* br = base + (3 * l + 0) * ABOX;
-        const double* bp = base + (3 * l + 1) * ABOX;
-        const double* bi = base + (3 * l + 2) * ABOX;
+        const double* bz = base + (2 * l + 0) * ABOX;
+        const double* bp = base + (2 * l + 1) * ABOX;
         double* pn = sm.pn + l * PN;
         for (int e = tid; e < PN; e += NT) {
           const int ry = e / PX, rx = e - ry * PX;
           const int bidx = ry * BX + rx + 1;
-          pn[e] = bi[bidx] * br[bidx] + bt * bp[bidx];
+          double zc = bz[bidx];
+          if (TL) zc += sm.cn[(ry == 0 ? 0 : (ry == BY - 1 ? 6 : 3)) + (rx == 0 ? 0 : (rx == PX - 1 ? 2 : 1))];
+          pn[e] = fma(bt, bp[bidx], zc);
         }
       }
       __syncthreads();
@@ -436,15 +545,62 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
 #pragma unroll
     for (int kk = 0; kk < 2 * L; ++kk) acc2[kk] = 0.0;
     const long long Np2 = Np >> 1;
+    if (TL) {
+      // tile by tile (same hand-out as phase A), so that P^T r of every tile
+      // is summed inside one CTA
+      const int lane = tid & 31, warp = tid >> 5;
+      for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+        const int w = t / tiles, tt = t - w * tiles;
+        int a0 = 0;
+#pragma unroll
+        for (int kk = 0; kk < L; ++kk) if (kk == w) a0 = act_list[kk];
+        const double al = S.alpha[a0];
+        const int gx = (tt % sp.tiles_x) * TX + lx, y0 = (tt / sp.tiles_x) * TY;
+        double* x = sp.p[a0];
+        double* r = sp.r[a0];
+        double* zz = sp.z[a0];
+        const double* Pn = sp.P[cur ^ 1][a0];
+        double rs = 0.0;
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          const int gy = y0 + ly + RPT * j;
+          if (gx >= nx || gy >= ny) continue;
+          const long long i = (long long)gy * pitch + gx;
+          const double rv = ldc(r + i) - al * ldc(sp.q[a0] + i);
+          const double xn = ldc(x + i) + al * ldc(Pn + i);
+          const double zv = ldr(sp.invd[a0] + i) * rv;
+          x[i] = xn;
+          r[i] = rv;
+          zz[i] = zv;
+#pragma unroll
+          for (int kk = 0; kk < L; ++kk)
+            if (kk == a0) {
+              acc2[kk] += rv * rv;
+              acc2[L + kk] += rv * zv;
+            }
+          rs += rv;
+        }
+        rs = warp_sum(rs);
+        if (lane == 0) sm.red[warp] = rs;
+        __syncthreads();
+        if (tid == 0) {
+          double g = 0.0;
+          for (int k2 = 0; k2 < NT / 32; ++k2) g += sm.red[k2];
+          sp.gsum[a0][tt] = g;
+        }
+        __syncthreads();
+      }
+    }
 #pragma unroll
     for (int a = 0; a < L; ++a) {
-      if (!(active & (1u << a))) continue;
+      if (TL || !(active & (1u << a))) continue;
       const double al = S.alpha[a];
       double2* x = reinterpret_cast<double2*>(sp.p[a]);
       double2* r = reinterpret_cast<double2*>(sp.r[a]);
       const double2* Pn = reinterpret_cast<const double2*>(sp.P[cur ^ 1][a]);
       const double2* qq = reinterpret_cast<const double2*>(sp.q[a]);
       const double2* iv = reinterpret_cast<const double2*>(sp.invd[a]);
+      double2* zz = reinterpret_cast<double2*>(sp.z[a]);
 #pragma unroll 2
       for (long long j = gtid; j < Np2; j += gstride) {
         const double2 rv0 = __ldcg(r + j);
@@ -452,15 +608,18 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
         const double2 xv = __ldcg(x + j);
         const double2 pv = __ldcg(Pn + j);
         const double2 dv = __ldg(iv + j);
-        double2 rv, xn;
+        double2 rv, xn, zv;
         rv.x = rv0.x - al * qv.x;
         rv.y = rv0.y - al * qv.y;
         xn.x = xv.x + al * pv.x;
         xn.y = xv.y + al * pv.y;
+        zv.x = dv.x * rv.x;
+        zv.y = dv.y * rv.y;
         x[j] = xn;
         r[j] = rv;
+        zz[j] = zv;
         acc2[a] += rv.x * rv.x + rv.y * rv.y;
-        acc2[L + a] += rv.x * (dv.x * rv.x) + rv.y * (dv.y * rv.y);
+        acc2[L + a] += rv.x * zv.x + rv.y * zv.y;
       }
     }
     block_store<2 * L>(acc2, qbits(active, L, 2), sm.box, sp.partials, slot);
@@ -478,8 +637,12 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
         const double rra = COUPLED ? s0 : sm.res[a];
         const double rzn = COUPLED ? s1 : sm.res[L + a];
         S.rr[a] = rra;
-        S.beta[a] = rzn / S.rz[a];
-        S.rz[a] = rzn;
+        if (TL) {
+          S.rzl[a] = rzn;  // beta after the coarse term
+        } else {
+          S.beta[a] = rzn / S.rz[a];
+          S.rz[a] = rzn;
+        }
         S.iters[a] = it;
         if (!(rra > rtol2 * S.bb[a])) act &= ~(1u << a);
         if (!isfinite(rra)) bad = 1;
@@ -493,6 +656,22 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_BREAKDOWN);
       ok = false;
       break;
+    }
+    if (TL && active) {
+      double gc[L];
+      coarse_correct<L>(sp, active, sm, gc);
+      block_store<L>(gc, active, sm.box, sp.partials, slot);
+      if (!grid_sync(sp)) { ok = false; break; }
+      grid_totals<L>(sp.partials, slot, sm.res);
+      slot ^= 1;
+      if (tid == 0)
+        for (int a = 0; a < L; ++a)
+          if (active & (1u << a)) {
+            const double rzn = S.rzl[a] + sm.res[a];
+            S.beta[a] = rzn / S.rz[a];
+            S.rz[a] = rzn;
+          }
+      __syncthreads();
     }
     cur ^= 1;
   }
@@ -509,7 +688,9 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
   // accurate.
   if (ok) {
     constexpr int NPAIR = L * (L - 1) / 2;
-    constexpr int NQC = COUPLED ? L + NPAIR : 2 * L;
+    // decoupled: [1^T r, 1^T diag(A0 - D)] per continuum; coupled:
+    // [1^T r per continuum, Q sums per pair, well sums per continuum]
+    constexpr int NQC = COUPLED ? 2 * L + NPAIR : 2 * L;
     double cs[NQC];
 #pragma unroll
     for (int kk = 0; kk < NQC; ++kk) cs[kk] = 0.0;
@@ -525,6 +706,11 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       for (int a = 0; a < L; ++a) {
         if (!(mask & (1u << a))) continue;
         double tv = ldr(sp.F[a] + i) + sp.mtau[a] * (ldc(sp.pprev[a] + i) - xv[a]);
+        if (sp.W[a]) {
+          const double wv = ldr(sp.W[a] + i);
+          tv += ldr(sp.FW[a] + i) - wv * xv[a];
+          if (COUPLED) cs[L + NPAIR + a] += wv;
+        }
 #pragma unroll
         for (int b = 0; b < L; ++b) {
           if (b == a) continue;
@@ -550,13 +736,13 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       slot ^= 1;
       double shift[L];
       if (COUPLED) {
-        // G_aa = N m_a/tau + sum_b Q_ab, G_ab = -Q_ab (Q summed over cells)
+        // G_aa = N m_a/tau + sum_b Q_ab + W_a, G_ab = -Q_ab (Q, W summed over cells)
         double G[L][L], c[L];
 #pragma unroll
         for (int a = 0; a < L; ++a) {
 #pragma unroll
           for (int b = 0; b < L; ++b) G[a][b] = 0.0;
-          G[a][a] = (double)sp.N * sp.mtau[a];
+          G[a][a] = (double)sp.N * sp.mtau[a] + ct[L + NPAIR + a];
           c[a] = ct[a];
         }
         int pi = 0;
@@ -626,15 +812,17 @@ template <int L, bool COUPLED>
 __global__ void __launch_bounds__(NT, 1)
     step_kernel(const __grid_constant__ StepParams sp, const __grid_constant__ TmaMaps maps) {
   constexpr int NL = COUPLED ? L : 1;
-  constexpr int NARR = 3 * NL;
+  constexpr int NARR = 2 * NL;
   constexpr int NST = nstage(L, COUPLED);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // TMA destinations need 128-B aligned slots: align the dynamic base.
   unsigned char* smem_base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   __shared__ Scal64 s_scal;
+  __shared__ double s_cn[9];
   Smem sm;
   sm.sc = &s_scal;
+  sm.cn = s_cn;
   sm.box = reinterpret_cast<double*>(smem_base);
   sm.pn = sm.box + NST * NARR * ABOX;
   sm.red = sm.pn + NL * PN;
@@ -672,8 +860,10 @@ __global__ void __launch_bounds__(NT, 1)
   if (!ok || done == 0) return;
 
   // ---- mass identity of the last step (Section 3.3, summed equations) ----
-  // sum_a m_a dp_a + tau sum_{a<b} q_ab (w_a dp_a + w_b dp_b) = tau sum F,
-  // with (w_a, w_b) = (1,1) D, (0,1) L, (1,0) U, (0,0) coupled.
+  // sum_a m_a dp_a + tau sum_{a<b} q_ab (w_a dp_a + w_b dp_b)
+  //   = tau sum (F + W (p_w - p^n)),
+  // with (w_a, w_b) = (1,1) D, (0,1) L, (1,0) U, (0,0) coupled; the implicit
+  // well term enters every scheme the same way.
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const double wa = (!COUPLED && (sp.scheme == MC_SCHEME_D || sp.scheme == MC_SCHEME_U)) ? 1.0 : 0.0;
   const double wb = (!COUPLED && (sp.scheme == MC_SCHEME_D || sp.scheme == MC_SCHEME_L)) ? 1.0 : 0.0;
@@ -683,7 +873,8 @@ __global__ void __launch_bounds__(NT, 1)
     for (int a = 0; a < L; ++a) {
       dp[a] = ldc(sp.p[a] + i) - ldc(sp.pprev[a] + i);
       const double m = sp.mass[a] * dp[a];
-      const double f = ldr(sp.F[a] + i);
+      double f = ldr(sp.F[a] + i);
+      if (sp.W[a]) f += ldr(sp.FW[a] + i) - ldr(sp.W[a] + i) * ldc(sp.p[a] + i);
       acc[0] += m;
       acc[1] += f;
       acc[3] += fabs(m) + sp.tau * fabs(f);
@@ -711,7 +902,7 @@ template <int L, bool C>
 constexpr size_t smem_bytes() {
   constexpr int NL = C ? L : 1;
   constexpr int NST = nstage(L, C);
-  return (size_t)(NST * 3 * NL * ABOX + NL * PN + (NT / 32) * KMAX + KMAX) * sizeof(double) +
+  return (size_t)(NST * 2 * NL * ABOX + NL * PN + (NT / 32) * KMAX + KMAX) * sizeof(double) +
          NST * sizeof(uint64_t) + 128;
 }
 
@@ -742,7 +933,56 @@ int max_blocks_for(KInfo k, int threads, int num_sms) {
   return per_sm * num_sms;
 }
 
+// A_c = P^T (M/tau + A0)_a P on the tile grid: one thread per coarse row I
+// sums diag(A0 - D) over the tile and the face transmissibilities across each
+// tile side; the off-diagonal entry to a neighbouring tile is minus that side's
+// sum (the same faces in the same order from both sides, so A_c is exactly
+// symmetric). Ac must be zero on entry.
+__global__ void coarse_assemble_kernel(int nx, int ny, int pitch, int tiles_x, int tiles_y,
+                                       const double* TE, const double* TN, const double* diagc,
+                                       double diagc_const, double* Ac) {
+  const int nc = tiles_x * tiles_y;
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+    const int x0 = (I % tiles_x) * TX, y0 = (I / tiles_x) * TY;
+    const int x1 = min(x0 + TX, nx), y1 = min(y0 + TY, ny);
+    double d = 0.0, te = 0.0, tw = 0.0, tn = 0.0, ts = 0.0;
+    for (int y = y0; y < y1; ++y)
+      for (int x = x0; x < x1; ++x) d += diagc ? diagc[(long long)y * pitch + x] : diagc_const;
+    for (int y = y0; y < y1; ++y) {
+      if (x1 < nx) te += TE[(long long)y * pitch + x1 - 1];
+      if (x0 > 0) tw += TE[(long long)y * pitch + x0 - 1];
+    }
+    for (int x = x0; x < x1; ++x) {
+      if (y1 < ny) tn += TN[(long long)(y1 - 1) * pitch + x];
+      if (y0 > 0) ts += TN[(long long)(y0 - 1) * pitch + x];
+    }
+    double* row = Ac + (long long)I * nc;
+    row[I] = d + te + tw + tn + ts;
+    if (x1 < nx) row[I + 1] = -te;
+    if (x0 > 0) row[I - 1] = -tw;
+    if (y1 < ny) row[I + tiles_x] = -tn;
+    if (y0 > 0) row[I - tiles_x] = -ts;
+  }
+}
+
 }  // namespace
+
+int mc_step_tiles(int nx, int ny) { return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY); }
+
+cudaError_t mc_launch_coarse_assemble(const mc_ctx* ctx, int a, double* Ac) {
+  const int tx = (ctx->nx + TX - 1) / TX, ty = (ctx->ny + TY - 1) / TY;
+  const long long nc = (long long)tx * ty;
+  cudaError_t e = cudaMemsetAsync(Ac, 0, (size_t)(nc * nc) * sizeof(double), ctx->stream);
+  if (e != cudaSuccess) return e;
+  double dconst = ctx->c[a] * ctx->h * ctx->h / ctx->tau;
+  for (int b = 0; b < ctx->L; ++b)
+    if (b != a) dconst += ctx->sigma[a][b] * ctx->h * ctx->h;
+  const int blocks = (int)((nc + 127) / 128);
+  coarse_assemble_kernel<<<blocks, 128, 0, ctx->stream>>>(ctx->nx, ctx->ny, ctx->pitch, tx, ty,
+                                                          ctx->TE[a], ctx->TN[a], ctx->diagc[a],
+                                                          dconst, Ac);
+  return cudaGetLastError();
+}
 
 int mc_step_max_blocks(int L, int threads, int num_sms) {
   const int a = max_blocks_for(pick(L, false), threads, num_sms);
