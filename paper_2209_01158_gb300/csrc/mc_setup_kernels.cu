@@ -178,11 +178,15 @@ cudaError_t mc_launch_diag(mc_ctx* ctx, int a) {
   return cudaGetLastError();
 }
 
+namespace {
+
 __global__ void well_kernel(long long Np, const double* __restrict__ W, double* __restrict__ FW) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Np;
        i += (long long)gridDim.x * blockDim.x)
     FW[i] = W[i] * FW[i];
 }
+
+}  // namespace
 
 cudaError_t mc_launch_well(mc_ctx* ctx, int a) {
   well_kernel<<<grid_for(ctx->Np), 256, 0, ctx->stream>>>(ctx->Np, ctx->W[a], ctx->FW[a]);

@@ -243,7 +243,7 @@ __device__ void coarse_correct(const StepParams& sp, unsigned act, Smem& sm, dou
 // One linear solve: the continua in `mask` (decoupled, independent systems),
 // or all L continua as one coupled system. Warm start from p, result in p.
 // Returns false when the run must stop (timeout, breakdown, no convergence).
-template <int L, bool COUPLED>
+template <int L, bool COUPLED, bool TLV>
 __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned mask, Smem& sm,
                           uint32_t& phb) {
   constexpr int NL = COUPLED ? L : 1;
@@ -323,7 +323,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
   int cur = 0;
   int slot = 1;
   bool ok = true;
-  const bool TL = !COUPLED && sp.two_level;
+  constexpr bool TL = !COUPLED && TLV;
   if (TL && active) {
     // z_0 = D^-1 r_0 + P c_0: the coarse term, and its share of (r_0, z_0)
     tile_rsums<L>(sp, active, sm);
@@ -808,7 +808,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
   return ok;
 }
 
-template <int L, bool COUPLED>
+template <int L, bool COUPLED, bool TLV>
 __global__ void __launch_bounds__(NT, 1)
     step_kernel(const __grid_constant__ StepParams sp, const __grid_constant__ TmaMaps maps) {
   constexpr int NL = COUPLED ? L : 1;
@@ -845,13 +845,13 @@ __global__ void __launch_bounds__(NT, 1)
     for (int a = 0; a < L; ++a)
       for (long long i = gtid; i < Np; i += gstride) sp.pprev[a][i] = ldc(sp.p[a] + i);
     if (COUPLED) {
-      ok = pcg_solve<L, true>(sp, maps, (1u << L) - 1u, sm, phb);
+      ok = pcg_solve<L, true, false>(sp, maps, (1u << L) - 1u, sm, phb);
     } else if (sp.scheme == MC_SCHEME_D) {
-      ok = pcg_solve<L, false>(sp, maps, (1u << L) - 1u, sm, phb);
+      ok = pcg_solve<L, false, TLV>(sp, maps, (1u << L) - 1u, sm, phb);
     } else {
       for (int k = 0; k < L && ok; ++k) {
         const int a = sp.scheme == MC_SCHEME_U ? L - 1 - k : k;
-        ok = pcg_solve<L, false>(sp, maps, 1u << a, sm, phb);
+        ok = pcg_solve<L, false, TLV>(sp, maps, 1u << a, sm, phb);
       }
     }
     if (ok) ++done;
@@ -911,17 +911,19 @@ struct KInfo {
   size_t smem;
 };
 
-template <int L, bool C>
+// The two-level variant is a separate instantiation, so that the Jacobi
+// kernel carries none of its code.
+template <int L, bool C, bool T>
 KInfo info() {
-  return KInfo{(void*)step_kernel<L, C>, smem_bytes<L, C>()};
+  return KInfo{(void*)step_kernel<L, C, T>, smem_bytes<L, C>()};
 }
 
-KInfo pick(int L, bool coupled) {
+KInfo pick(int L, bool coupled, bool two_level = false) {
   switch (L) {
-    case 1: return coupled ? info<1, true>() : info<1, false>();
-    case 2: return coupled ? info<2, true>() : info<2, false>();
-    case 3: return coupled ? info<3, true>() : info<3, false>();
-    default: return coupled ? info<4, true>() : info<4, false>();
+    case 1: return coupled ? info<1, true, false>() : (two_level ? info<1, false, true>() : info<1, false, false>());
+    case 2: return coupled ? info<2, true, false>() : (two_level ? info<2, false, true>() : info<2, false, false>());
+    case 3: return coupled ? info<3, true, false>() : (two_level ? info<3, false, true>() : info<3, false, false>());
+    default: return coupled ? info<4, true, false>() : (two_level ? info<4, false, true>() : info<4, false, false>());
   }
 }
 
@@ -985,7 +987,9 @@ cudaError_t mc_launch_coarse_assemble(const mc_ctx* ctx, int a, double* Ac) {
 }
 
 int mc_step_max_blocks(int L, int threads, int num_sms) {
-  const int a = max_blocks_for(pick(L, false), threads, num_sms);
+  const int a0 = max_blocks_for(pick(L, false), threads, num_sms);
+  const int a1 = max_blocks_for(pick(L, false, true), threads, num_sms);
+  const int a = a0 < a1 ? a0 : a1;
   const int b = max_blocks_for(pick(L, true), threads, num_sms);
   return a < b ? a : b;
 }
@@ -999,7 +1003,7 @@ cudaError_t mc_launch_steps_raw(const StepParams& sp_in, const TmaMaps& maps_in,
   TmaMaps maps = maps_in;
   sp.tiles_x = (sp.nx + TX - 1) / TX;
   sp.tiles_y = (sp.ny + TY - 1) / TY;
-  KInfo k = pick(sp.L, sp.scheme == MC_SCHEME_COUPLED);
+  KInfo k = pick(sp.L, sp.scheme == MC_SCHEME_COUPLED, sp.two_level != 0);
   cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
   if (e != cudaSuccess) return e;
   void* args[] = {&sp, &maps};
