@@ -55,14 +55,16 @@ def test_struct_layout_matches_c(tmp_path):
     import ctypes
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mc.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(mc_opts), sizeof(mc_stats),'
-                   ' sizeof(mc_grid), offsetof(mc_stats, rel_residual), offsetof(mc_opts, spin_limit));'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mc_opts), sizeof(mc_stats),'
+                   ' sizeof(mc_grid), offsetof(mc_stats, rel_residual), offsetof(mc_opts, spin_limit),'
+                   ' offsetof(mc_opts, inner_form), offsetof(mc_stats, mass_defect));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert vals == [ctypes.sizeof(N.mc_opts), ctypes.sizeof(N.mc_stats), ctypes.sizeof(N.mc_grid),
-                    N.mc_stats.rel_residual.offset, N.mc_opts.spin_limit.offset]
+                    N.mc_stats.rel_residual.offset, N.mc_opts.spin_limit.offset,
+                    N.mc_opts.inner_form.offset, N.mc_stats.mass_defect.offset]
 
 
 def test_host_only_calls(lib):
