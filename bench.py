@@ -53,6 +53,12 @@ def inner_bytes_per_cell_it(precision, inner_form):
     n_t, n_other = 2, (9 if inner_form == 1 else 11)
     return n_t * (2 if precision == 2 else 4) + 4 * n_other
 RTOL_D = 1e-10
+METRIC = "continuum-cell updates/s (D-scheme at rel-L2 1e-8) and roofline fraction"
+
+
+def workload_name(n):
+    return ("triple_1024: 3 continua, %dx%d, tau=1/200, D-scheme FP64, rtol %g"
+            % (n, n, RTOL_D))
 RTOL_COUPLED = 1e-11
 RTOL_BATCH = 1e-12           # fracture continua: rtol 1e-10 leaves errors up to ~3e-8
 SMI_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -220,12 +226,12 @@ def run_reference(args, ws, rank):
     w = crop(mi.triple_1024(n=args.n), args.crop)
     val, dt, tf = oracle_timing(w, args.steps, args.warmup)
     line = {
-        "impl": "reference", "metric": "continuum-cell updates/s (D-scheme, rel-L2 1e-8)",
+        "impl": "reference", "metric": METRIC,
         "value": val, "unit": "continuum-cell updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "triple_1024 (3 continua, 1024x1024, tau=1/200), D-scheme",
-                   "sample": "%dx%d crop" % (w.nx, w.ny)},
+        "config": {"workload": workload_name(args.n),
+                   "sample": "%dx%d crop, oracle direct solves" % (w.nx, w.ny)},
         "cpu_baseline": {"value": val, "unit": "continuum-cell updates/s", "cores": 1, "kind": "oracle",
                          "sample": "oracle D-scheme (SuperLU + extended-precision refinement), %dx%d "
                                    "crop of the 1024x1024 workload, %d steps after %d warm-up; "
@@ -558,13 +564,12 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "continuum-cell updates/s (D-scheme at rel-L2 1e-8) and roofline fraction",
+            "metric": METRIC,
             "value": value, "unit": "continuum-cell updates/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dev_time / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded correlated log-normal fields)",
-            "config": {"workload": "triple_1024: 3 continua, 1024x1024, tau=1/200, D-scheme FP64, "
-                                   "rtol %g" % RTOL_D,
+            "config": {"workload": workload_name(args.n),
                        "l2": "working set %.0f MB > 129 MB L2 (no flush)" % (8 * L * Ncell * 11 / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "pcg_iterations_per_step": float(np.mean(its))},
