@@ -65,3 +65,18 @@ def test_coupled_step_full_size_residual_and_mass(setup):
     rhs = o.tau * metrics.total_source(F)
     scale = o.tau * sum(np.abs(f).sum() for f in F)
     assert abs(lhs - rhs) <= 1e-9 * scale
+
+
+def test_two_level_d_scheme_full_size(setup):
+    """The two-level preconditioner option in the benchmark's configuration:
+    two D-scheme steps at 1024^2 against the oracle (FP64 bar)."""
+    m, w, o, F, ref = setup
+    opts = m.mc_default_opts()
+    opts.rtol = 1e-12
+    opts.precond = m.N.MC_PRECOND_TWO_LEVEL
+    ctx = m.Context.from_workload(w, opts=opts)
+    st = ctx.step("D", 2)
+    p = ctx.get_state()
+    ctx.close()
+    err = metrics.rel_l2(ref, p)
+    assert err <= 1e-10, (err, st)
