@@ -23,9 +23,12 @@
 //      vectors, Jacobi), to a relative residual inner_rtol; the dot products
 //      are summed per thread in FP32 and then across the grid in FP64;
 //   5. x += d in FP64.
-// The inner iteration has the structure of the FP64 kernel (TMA halo tiles of
-// r, P_old and invd in a shared-memory ring, then a pointwise vector phase),
-// with 4-byte data.
+// The inner PCG runs in one of two forms (mc_opts.inner_form): the default
+// single-reduction recurrences (`inner_single`: one tile pass and one grid
+// reduction per iteration, halo values recomputed from double-buffered
+// vectors), or the two-reduction textbook recurrences with the structure of
+// the FP64 kernel (TMA halo tiles of r, P_old and invd in a shared-memory
+// ring, then a pointwise vector phase), with 4-byte data.
 
 #include <cuda_bf16.h>
 #include <math.h>
