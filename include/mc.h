@@ -161,9 +161,9 @@ mc_status mc_set_source(mc_ctx* ctx, int32_t alpha, const double* F);
  *   W   host nx*ny cell-integrated well indices (>= 0, finite; 0 outside the
  *       wells), or NULL to remove the wells of alpha.
  *   pw  host nx*ny well pressures (finite); ignored when W is NULL.
- *   The arrays are copied. Contexts with wells are not accepted by
- *   mc_nlmc_build (MC_E_STATE); a batch sees the wells its contexts had when
- *   mc_batch_create ran. MC_E_ARG on a bad alpha or data.
+ *   The arrays are copied. The NLMC coarse model built on the context takes
+ *   the wells it has at build time; a batch sees the wells its contexts had
+ *   when mc_batch_create ran. MC_E_ARG on a bad alpha or data.
  */
 mc_status mc_set_well(mc_ctx* ctx, int32_t alpha, const double* W, const double* pw);
 
@@ -235,17 +235,57 @@ mc_status mc_device_bytes(const mc_ctx* ctx, int64_t* bytes);
  *   preconditioned-residual reduction basis_rtol (at most basis_max_iter
  *   iterations; MC_E_NOCONV otherwise).
  *   Coarse operator: A_bar = R (D + Q) R^T; M_bar = diag(c_a |K_i|);
- *   F_bar = block sums of the context's current sources; the coarse state
- *   starts as the block means of the context's current state.
+ *   F_bar = block sums of the context's current sources; wells of the
+ *   context (mc_set_well) enter as W_bar = diag(block sums of W) and the
+ *   right-hand side block sums of W p_w (the coarse finite-volume form of
+ *   Section 4.1 for piecewise-constant data); the coarse state starts as the
+ *   block means of the context's current state.
  * Coarse index (alpha, i) -> alpha * ncx*ncy + i, i = J*ncx + I.
- * The context must outlive the returned object.
+ * The context must outlive the returned object. Same as mc_nlmc_build_ex
+ * with support NULL and flags 0.
  */
 mc_status mc_nlmc_build(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
                         double basis_rtol, int32_t basis_max_iter, mc_nlmc** out);
 
+/* Conservative coarse operator: after A_bar = R (D + Q) R^T, every diagonal
+ * entry is set to minus the sum of the other entries of its row, so that
+ * A_bar 1 = 0 and the coarse model conserves mass like the fine finite-volume
+ * one. The exact (globally oversampled) basis reproduces constants and has
+ * this property; local oversampling truncates the basis functions and breaks
+ * it, and with very permeable fractures the defect outweighs the coarse mass
+ * term (a constant state drifts). */
+#define MC_NLMC_CONSERVATIVE 1
+
+/*
+ * mc_nlmc_build_ex -- mc_nlmc_build for continua that live on part of the
+ *   domain (Section 4.1: the constraint of continuum alpha averages over
+ *   K_j^alpha = Omega_alpha ∩ K_j).
+ *   support  NULL (every continuum covers the domain), or L host pointers,
+ *            each NULL (that continuum covers the domain) or nx*ny bytes,
+ *            nonzero on the cells of Omega_alpha (an embedded fracture
+ *            continuum: the cells its fractures cross). Copied.
+ *   flags    0 or MC_NLMC_CONSERVATIVE.
+ *   With a support mask, the mean constraints, M_bar = diag(c_a |K_i^alpha|),
+ *   the coarse wells and the initial coarse state (means of p_alpha) run over
+ *   K_i^alpha; cells of continuum alpha outside Omega_alpha are unconstrained
+ *   in every basis function. A block with no cell of Omega_alpha has no coarse
+ *   unknown of continuum alpha: no basis function, zero rows and columns of
+ *   A_bar, M_bar = F_bar = 0, and its entry of the coarse state is held at 0
+ *   by every coarse step (mc_nlmc_active lists the unknowns that exist). The
+ *   coarse layout stays L * ncx * ncy.
+ */
+mc_status mc_nlmc_build_ex(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
+                           double basis_rtol, int32_t basis_max_iter,
+                           const uint8_t* const* support, int32_t flags, mc_nlmc** out);
+
+/* active[k] = 1 where coarse unknown k (L * ncx * ncy, host bytes) exists,
+ * 0 where its block holds no cell of that continuum's support. */
+mc_status mc_nlmc_active(mc_nlmc* m, uint8_t* active);
+
 /* nsteps coarse steps: MC_SCHEME_COUPLED (Eq. is-nlmc) or the D-, L-,
  * U-schemes of Section 4.3 (A0_bar = diagonal / lower / upper blocks of
- * A_bar). Each coarse solve: explicit inverse (formed once) + one residual
+ * A_bar), with the coarse wells implicit in every scheme (like the fine
+ * ones). Each coarse solve: explicit inverse (formed once) + one residual
  * correction. stats: steps_done, status. */
 mc_status mc_nlmc_step(mc_nlmc* m, int32_t scheme, int32_t nsteps, mc_stats* stats);
 
@@ -391,6 +431,17 @@ mc_status mc_step_single_noalloc(int32_t nx, int32_t ny, const double* k, double
                                  double tau, const double* F, double* p, int32_t nsteps,
                                  double rtol, int32_t max_iter, void* stream,
                                  mc_stats* stats);
+
+/*
+ * mc_fp64_fma_rate -- measurement utility (the paper has no counterpart):
+ *   the FP64 fused-multiply-add throughput of the current device in
+ *   TFLOP/s (2 FLOP per FMA), from a register-only kernel of independent FMA
+ *   chains on every SM, timed with CUDA events on `stream` (NULL: legacy
+ *   default) after one warm-up launch. It is the denominator of the FP64
+ *   step kernel's roofline. Allocates and frees a small output buffer on the
+ *   stream; synchronises it.
+ */
+mc_status mc_fp64_fma_rate(void* stream, double* tflops);
 
 void mc_destroy(mc_ctx* ctx);
 

@@ -37,6 +37,10 @@ class Workload:
     wells: Dict[int, Tuple[np.ndarray, np.ndarray]] = field(default_factory=dict)
     coarse: Optional[Tuple[int, int, int]] = None   # (ncx, ncy, layers)
     seed: Optional[int] = None
+    # continuum -> boolean (ny, nx) cells where the continuum physically lives
+    # (an embedded fracture continuum: the cells its segments cross); absent
+    # continua cover the whole domain
+    support: Dict[int, np.ndarray] = field(default_factory=dict)
 
     @property
     def h(self):
@@ -154,7 +158,8 @@ def fracture_instance(seed, n=None, L=None, tau=1.0 / 100, nsteps=100,
         sc = {(0, 2): sig_f, (1, 2): sig_f.copy()}
     return Workload("fracture_%d_L%d_s%d" % (n, L, seed), n, n, L, k, c, sigma,
                     tau, nsteps, _fracture_sources(ell, n, L),
-                    [np.zeros((n, n))] * L, sigma_cell=sc, seed=seed)
+                    [np.zeros((n, n))] * L, sigma_cell=sc, seed=seed,
+                    support={L - 1: ell > 0.0})
 
 
 def batched_instances(count=256, base_seed=4000, sizes=(128, 256, 512, 1024),
@@ -227,7 +232,7 @@ def paper_wells(L=2, n=200, seed=None, nsteps=50, qw=1e5, pw=1.2):
     tau = 0.002 / nsteps
     w = Workload("paper%dC_%d" % (L, n), n, n, L, k, c, sigma, tau, nsteps,
                  [np.zeros((n, n)) for _ in range(L)], [np.ones((n, n)) for _ in range(L)],
-                 sigma_cell=sc, seed=seed)
+                 sigma_cell=sc, seed=seed, support={L - 1: ell > 0.0})
     w.wells = {L - 1: (W, np.full((n, n), pw))}
     return w
 

@@ -9,8 +9,16 @@ boundary, plus Lagrange multipliers that impose
 
     mean of psi_alpha over K_j = delta_ij delta_alpha,beta
 
-for every coarse block K_j inside K_i^+ and every continuum alpha (co-located
-continua: K_j^alpha = K_j). The KKT matrix is factorised directly.
+for every coarse block K_j inside K_i^+ and every continuum alpha. The mean
+runs over K_j^alpha = Omega_alpha intersected with K_j (Section 4.1): by
+default Omega_alpha is the whole domain (co-located continua), and `support`
+gives Omega_alpha as a set of fine cells for continua that live only on part
+of it (an embedded fracture continuum: its fracture cells). A block holding
+no cell of Omega_alpha has no coarse unknown for that continuum (the paper
+counts 400 matrix + 162 fracture unknowns on its 20 x 20 coarse grid): no
+basis function, no constraint, and its entry of every coarse vector is
+inert (zero rows and columns of R and A_bar, state held at 0). The KKT
+matrix is factorised directly.
 
 R stacks the basis functions: row (beta, i) = psi^{i,beta}, columns in the
 fine continuum-major order. The coarse operator is A_bar = R A R^T with A the
@@ -23,8 +31,24 @@ Readings:
     `dirichlet_on_domain=True` applies the Dirichlet condition literally on
     the whole region boundary.
   * M_bar and F_bar are the coarse finite-volume forms the paper gives for
-    piecewise-constant data: M_bar_alpha = diag(c_alpha |K_i|), F_bar = sums
-    of the fine cell-integrated sources over each block.
+    piecewise-constant data: M_bar_alpha = diag(c_alpha |K_i^alpha|), F_bar =
+    sums of the fine cell-integrated sources over each block. The coarse
+    unknown of (alpha, K_i) is the mean of p_alpha over K_i^alpha, so the
+    initial coarse state and the reference of e_H take that mean.
+  * Wells (the implicit relaxation W (p_w - p) of the fine model) enter the
+    coarse model in the same coarse finite-volume form as the sources:
+    W_bar = diag(sum of W over K_i^alpha) joins the continuum's diagonal
+    block and W_bar-weighted p_w (sum of W p_w over K_i^alpha) its
+    right-hand side.
+  * Conservative option (`conservative=True`). The exact multiscale space
+    (global oversampling) holds the constants, so A_bar 1 = 0 and the coarse
+    model conserves mass like the fine finite-volume one (the paper states
+    the coarse system keeps the finite-volume properties). Local oversampling
+    breaks this by the truncation of the basis functions; with a 1e6
+    fracture permeability the defect A_bar 1 is far larger than the coarse
+    mass term and drags a constant state away. The option restores it by
+    setting every diagonal entry to minus the sum of the row's other
+    entries (the off-diagonal coarse transmissibilities are kept).
   * Coarse schemes (Section 4.2-4.3): coupled Eq. is-nlmc; D-scheme with
     A0_bar = blockdiag(A_bar_aa); L/U schemes with the lower / upper block
     triangle of A_bar, continua in ascending / descending index order.
@@ -43,7 +67,8 @@ from .fv import diffusion_matrix
 
 
 class NLMC:
-    def __init__(self, fv, tau, ncx, ncy, layers, dirichlet_on_domain=False):
+    def __init__(self, fv, tau, ncx, ncy, layers, dirichlet_on_domain=False, support=None,
+                 conservative=False):
         nx, ny, L = fv.nx, fv.ny, fv.L
         if nx % ncx or ny % ncy:
             raise ValueError("coarse grid must divide the fine grid")
@@ -52,6 +77,11 @@ class NLMC:
         self.bx, self.by = nx // ncx, ny // ncy
         self.Nc = ncx * ncy
         self.dirichlet_on_domain = dirichlet_on_domain
+        self.sup = self.block_support(support)
+        # n_sup[a][j]: cells of K_j^alpha; active: coarse unknowns that exist
+        self.n_sup = [self.sup[a].reshape(ncy, self.by, ncx, self.bx).sum(axis=(1, 3)).ravel()
+                      for a in range(L)]
+        self.active = np.concatenate([self.n_sup[a] > 0 for a in range(L)])
         rr, cc, vv = [], [], []
         self.constraint_residual = 0.0
         for J in range(ncy):
@@ -59,6 +89,8 @@ class NLMC:
                 psis, cres = self.local_basis(I, J)
                 self.constraint_residual = max(self.constraint_residual, cres)
                 for beta in range(L):
+                    if psis[beta] is None:
+                        continue
                     cols, vals = psis[beta]
                     rr.append(np.full(cols.size, beta * self.Nc + J * ncx + I))
                     cc.append(cols)
@@ -67,9 +99,37 @@ class NLMC:
                                shape=(L * self.Nc, L * fv.N))
         A = fv.A()
         self.Abar = (self.R @ A @ self.R.T).toarray()
-        area = self.bx * self.by * fv.area
-        self.mbar = np.concatenate([np.full(self.Nc, fv.c[a] * area) for a in range(L)])
+        self.conservative = conservative
+        if conservative:
+            # restore A_bar 1 = 0 (mass conservation of the coarse model)
+            rs = self.Abar.sum(axis=1)
+            self.Abar[np.diag_indices_from(self.Abar)] -= rs
+        self.mbar = np.concatenate([fv.c[a] * fv.area * self.n_sup[a] for a in range(L)])
+        # coarse wells: W summed over K_j^alpha, and W p_w summed the same way
+        self.wbar = self._sup_sum([fv.W[a] for a in range(L)])
+        self.wpbar = self._sup_sum([fv.well_rhs(a) for a in range(L)])
         self._fact = {}
+
+    def block_support(self, support):
+        """Omega_alpha as L boolean (ny, nx) fields (all cells where no
+        support is given); K_j^alpha is its part inside block K_j."""
+        fv = self.fv
+        out = []
+        for a in range(fv.L):
+            s = None if support is None else support[a]
+            if s is None:
+                out.append(np.ones((fv.ny, fv.nx), dtype=bool))
+            else:
+                out.append(np.asarray(s, dtype=bool).reshape(fv.ny, fv.nx).copy())
+        return out
+
+    def _sup_sum(self, fields):
+        """Sums of L fine fields over K_j^alpha, continuum-major."""
+        fv = self.fv
+        return np.concatenate([
+            np.where(self.sup[a], np.asarray(fields[a]).reshape(fv.ny, fv.nx), 0.0)
+            .reshape(self.ncy, self.by, self.ncx, self.bx).sum(axis=(1, 3)).ravel()
+            for a in range(fv.L)])
 
     # -- region geometry ---------------------------------------------------
     def region(self, I, J):
@@ -110,22 +170,28 @@ class NLMC:
         return sp.bmat(blocks, format="csc"), lnx, lny
 
     def constraints(self, I0, I1, J0, J1):
-        """C: one row per (alpha, coarse block in the region), the block mean."""
+        """C: one row per (alpha, coarse block K_j in the region), the mean of
+        psi_alpha over K_j^alpha."""
         L = self.fv.L
-        lnx = (I1 - I0) * self.bx
-        lny = (J1 - J0) * self.by
+        x0, x1, y0, y1 = I0 * self.bx, I1 * self.bx, J0 * self.by, J1 * self.by
+        lnx = x1 - x0
+        lny = y1 - y0
         nloc = lnx * lny
         nb = (I1 - I0) * (J1 - J0)
-        inv = 1.0 / (self.bx * self.by)
-        rows, cols = [], []
+        rows, cols, vals = [], [], []
         lj, li = np.divmod(np.arange(nloc), lnx)
         blk = (lj // self.by) * (I1 - I0) + (li // self.bx)
+        gblk = (J0 + lj // self.by) * self.ncx + (I0 + li // self.bx)
         for a in range(L):
-            rows.append(a * nb + blk)
-            cols.append(a * nloc + np.arange(nloc))
-        C = sp.csr_matrix((np.full(L * nloc, inv), (np.concatenate(rows), np.concatenate(cols))),
+            on = self.sup[a][y0:y1, x0:x1].ravel()
+            rows.append(a * nb + blk[on])
+            cols.append(a * nloc + np.arange(nloc)[on])
+            vals.append(1.0 / self.n_sup[a][gblk[on]])
+        C = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                           shape=(L * nb, L * nloc))
-        return C, nb
+        # one row per coarse unknown that exists (blocks without K_j^alpha drop out)
+        keep = np.flatnonzero(np.diff(C.indptr) > 0)
+        return C[keep], keep
 
     def local_basis(self, I, J):
         """psi^{i,beta} for beta = 0..L-1 by a direct KKT solve (Eq. eq:basis).
@@ -133,7 +199,8 @@ class NLMC:
         fv, L = self.fv, self.fv.L
         I0, I1, J0, J1 = self.region(I, J)
         A, lnx, lny = self.local_operator(I0, I1, J0, J1)
-        C, nb = self.constraints(I0, I1, J0, J1)
+        C, rowid = self.constraints(I0, I1, J0, J1)
+        nb = (I1 - I0) * (J1 - J0)
         nloc = lnx * lny
         K = sp.bmat([[A, C.T], [C, None]], format="csc")
         lu = splu(K)
@@ -143,9 +210,14 @@ class NLMC:
         gcell = (y0 + lj) * fv.nx + (x0 + li)
         out = []
         cres = 0.0
+        nc = rowid.size
         for beta in range(L):
-            rhs = np.zeros(L * nloc + L * nb)
-            rhs[L * nloc + beta * nb + centre] = 1.0
+            hit = np.flatnonzero(rowid == beta * nb + centre)
+            if hit.size == 0:   # K_i^beta is empty: no coarse unknown, no basis
+                out.append(None)
+                continue
+            rhs = np.zeros(L * nloc + nc)
+            rhs[L * nloc + hit[0]] = 1.0
             sol = lu.solve(rhs)
             for _ in range(2):
                 sol = sol + lu.solve(rhs - K @ sol)
@@ -158,32 +230,42 @@ class NLMC:
 
     # -- coarse data ---------------------------------------------------------
     def coarse_source(self, F):
+        """Block sums of the fine cell-integrated sources (0 for coarse
+        unknowns that do not exist)."""
         fv = self.fv
-        return np.concatenate([
+        f = np.concatenate([
             np.asarray(F[a]).reshape(fv.ny, fv.nx)
             .reshape(self.ncy, self.by, self.ncx, self.bx).sum(axis=(1, 3)).ravel()
             for a in range(fv.L)])
+        return np.where(self.active, f, 0.0)
 
     def coarse_mean(self, p):
+        """Mean of p_alpha over K_j^alpha for every block and continuum."""
         fv = self.fv
-        return np.concatenate([
-            np.asarray(p[a]).reshape(fv.ny, fv.nx)
-            .reshape(self.ncy, self.by, self.ncx, self.bx).mean(axis=(1, 3)).ravel()
-            for a in range(fv.L)])
+        out = []
+        for a in range(fv.L):
+            v = np.where(self.sup[a], np.asarray(p[a]).reshape(fv.ny, fv.nx), 0.0)
+            s = v.reshape(self.ncy, self.by, self.ncx, self.bx).sum(axis=(1, 3)).ravel()
+            out.append(np.divide(s, self.n_sup[a], out=np.zeros_like(s), where=self.n_sup[a] > 0))
+        return np.concatenate(out)
 
     def block(self, a, b):
         n = self.Nc
         return self.Abar[a * n:(a + 1) * n, b * n:(b + 1) * n]
 
     # -- coarse time schemes ---------------------------------------------------
+    def _idx(self, key):
+        """Coarse unknowns that exist, of all continua or of continuum key."""
+        n = self.Nc
+        if key == "coupled":
+            return np.flatnonzero(self.active)
+        return key * n + np.flatnonzero(self.active[key * n:(key + 1) * n])
+
     def _lu(self, key):
         if key not in self._fact:
-            n = self.Nc
-            if key == "coupled":
-                Mt = np.diag(self.mbar / self.tau) + self.Abar
-            else:
-                a = key
-                Mt = np.diag(self.mbar[a * n:(a + 1) * n] / self.tau) + self.block(a, a)
+            ix = self._idx(key)
+            d = self.mbar[ix] / self.tau + self.wbar[ix]
+            Mt = np.diag(d) + self.Abar[np.ix_(ix, ix)]
             self._fact[key] = (Mt, la.lu_factor(Mt))
         return self._fact[key]
 
@@ -200,26 +282,34 @@ class NLMC:
         return x
 
     def step(self, pbar, Fbar, scheme="D"):
+        """One coarse step; entries of unknowns that do not exist are 0
+        (their rows and columns of A_bar are zero)."""
         n, L = self.Nc, self.fv.L
+        b0 = self.mbar / self.tau * pbar + Fbar + self.wpbar
+        out = np.zeros(L * n)
         if scheme == "coupled":
-            return self._solve("coupled", self.mbar / self.tau * pbar + Fbar)
+            ix = self._idx("coupled")
+            out[ix] = self._solve("coupled", b0[ix])
+            return out
         if scheme in ("D", "L"):
             order = list(range(L))
         elif scheme == "U":
             order = list(range(L - 1, -1, -1))
         else:
             raise ValueError(scheme)
-        new = [None] * L
+        done = [False] * L
         for a in order:
             sl = slice(a * n, (a + 1) * n)
-            rhs = self.mbar[sl] / self.tau * pbar[sl] + Fbar[sl]
+            rhs = b0[sl].copy()
             for b in range(L):
                 if b == a:
                     continue
-                src = new[b] if (scheme != "D" and new[b] is not None) else pbar[b * n:(b + 1) * n]
-                rhs = rhs - self.block(a, b) @ src
-            new[a] = self._solve(a, rhs)
-        return np.concatenate(new)
+                src = out if (scheme != "D" and done[b]) else pbar
+                rhs = rhs - self.block(a, b) @ src[b * n:(b + 1) * n]
+            ix = self._idx(a)
+            out[ix] = self._solve(a, rhs[ix - a * n])
+            done[a] = True
+        return out
 
     def run(self, p0, F, nsteps, scheme="D", keep=False):
         pbar = self.coarse_mean(p0)

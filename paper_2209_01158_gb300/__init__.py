@@ -241,23 +241,56 @@ def mc_step_single_noalloc(nx, ny, k, c, tau, F, p, nsteps, rtol=1e-12, max_iter
     return d
 
 
+def mc_fp64_fma_rate(stream=None):
+    """Measured FP64 FMA throughput of the current device, TFLOP/s."""
+    v = C.c_double()
+    st = _lib().mc_fp64_fma_rate(_stream_handle(stream), C.byref(v))
+    if st != N.MC_OK:
+        raise MCError(st, _lib().mc_status_string(st).decode())
+    return v.value
+
+
 def mc_destroy(ctx):
     if ctx:
         _lib().mc_destroy(ctx)
 
 
 class NLMC:
-    """Owning wrapper of an mc_nlmc built on a Context (which must stay open)."""
+    """Owning wrapper of an mc_nlmc built on a Context (which must stay open).
 
-    def __init__(self, ctx, ncx, ncy, layers, basis_rtol=1e-12, basis_max_iter=50000):
+    support: None, or a list of L entries, each None or a boolean nx*ny mask
+    of the cells where that continuum lives (mc_nlmc_build_ex);
+    conservative: set MC_NLMC_CONSERVATIVE."""
+
+    def __init__(self, ctx, ncx, ncy, layers, basis_rtol=1e-12, basis_max_iter=50000,
+                 support=None, conservative=False):
         self.ctx = ctx
         self.ncx, self.ncy, self.L = int(ncx), int(ncy), ctx.L
         self.n = self.L * self.ncx * self.ncy
         h = C.c_void_p()
-        st = _lib().mc_nlmc_build(ctx.handle, int(ncx), int(ncy), int(layers), float(basis_rtol),
-                                  int(basis_max_iter), C.byref(h))
+        sup_arr, keep = None, []
+        if support is not None:
+            ptrs = []
+            for s in support:
+                if s is None:
+                    ptrs.append(None)
+                    continue
+                a = np.ascontiguousarray(np.ravel(s), dtype=np.uint8)
+                if a.size != ctx.n:
+                    raise ValueError("support mask needs nx*ny values")
+                keep.append(a)
+                ptrs.append(a.ctypes.data_as(C.c_void_p))
+            sup_arr = (C.c_void_p * len(ptrs))(*ptrs)
+        flags = N.MC_NLMC_CONSERVATIVE if conservative else 0
+        st = _lib().mc_nlmc_build_ex(ctx.handle, int(ncx), int(ncy), int(layers), float(basis_rtol),
+                                     int(basis_max_iter), sup_arr, int(flags), C.byref(h))
         _check(st, ctx.handle)
         self._h = h
+
+    def active(self):
+        out = np.empty(self.n, dtype=np.uint8)
+        _check(_lib().mc_nlmc_active(self._h, out.ctypes.data_as(C.POINTER(C.c_uint8))))
+        return out.astype(bool)
 
     def step(self, scheme="D", nsteps=1):
         sc = SCHEMES[scheme] if isinstance(scheme, str) else scheme

@@ -16,6 +16,7 @@ MC_PREC_FP64, MC_PREC_FP32_IR, MC_PREC_BF16T_IR = 0, 1, 2
 MC_PRECOND_JACOBI, MC_PRECOND_TWO_LEVEL = 0, 1
 MC_TWO_LEVEL_MAX_TILES = 2048
 MC_INNER_SINGLE_REDUCTION, MC_INNER_TWO_REDUCTIONS = 0, 1
+MC_NLMC_CONSERVATIVE = 1
 MC_SCHEME_COUPLED, MC_SCHEME_D, MC_SCHEME_L, MC_SCHEME_U = -1, 0, 1, 2
 
 dp = C.POINTER(C.c_double)
@@ -67,6 +68,10 @@ SIGNATURES = {
                                          C.POINTER(mc_stats)]),
     "mc_nlmc_build": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                 C.c_int32, C.POINTER(C.c_void_p)]),
+    "mc_nlmc_build_ex": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                   C.c_int32, C.POINTER(C.c_void_p), C.c_int32,
+                                   C.POINTER(C.c_void_p)]),
+    "mc_nlmc_active": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint8)]),
     "mc_nlmc_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(mc_stats)]),
     "mc_nlmc_set_state": (C.c_int, [C.c_void_p, dp]),
     "mc_nlmc_get_state": (C.c_int, [C.c_void_p, dp]),
@@ -84,6 +89,7 @@ SIGNATURES = {
     "mc_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "mc_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "mc_batch_destroy": (None, [C.c_void_p]),
+    "mc_fp64_fma_rate": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mc_destroy": (None, [C.c_void_p]),
     "mc_last_error": (C.c_char_p, [C.c_void_p]),
     "mc_status_string": (C.c_char_p, [C.c_int]),

@@ -388,17 +388,20 @@ mc_status mc_set_well(mc_ctx* ctx, int32_t alpha, const double* W, const double*
   CK(cudaSetDevice(ctx->device));
   const size_t fb = (size_t)ctx->Np * sizeof(double);
   if (W) {
-    if (!ctx->W[alpha]) {
-      CK(mc_alloc(ctx, (void**)&ctx->W[alpha], fb));
-      CK(mc_alloc(ctx, (void**)&ctx->FW[alpha], fb));
+    if (!ctx->W_buf[alpha]) {
+      CK(mc_alloc(ctx, (void**)&ctx->W_buf[alpha], fb));
+      CK(mc_alloc(ctx, (void**)&ctx->FW_buf[alpha], fb));
     }
     // the well makes diag(A0 - D) vary per cell
     if (!ctx->diagc[alpha]) CK(mc_alloc(ctx, (void**)&ctx->diagc[alpha], fb));
+    ctx->W[alpha] = ctx->W_buf[alpha];
+    ctx->FW[alpha] = ctx->FW_buf[alpha];
     CK(h2d(ctx, ctx->W[alpha], W));
     CK(h2d(ctx, ctx->FW[alpha], pw));
     CK(mc_launch_well(ctx, alpha));
   } else {
-    ctx->W[alpha] = nullptr;  // the buffers stay allocated until mc_destroy
+    // out of effect; the buffers are kept for a later mc_set_well
+    ctx->W[alpha] = nullptr;
     ctx->FW[alpha] = nullptr;
   }
   CK(mc_launch_diag(ctx, alpha));

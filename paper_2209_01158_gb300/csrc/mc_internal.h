@@ -149,8 +149,10 @@ struct mc_ctx {
   double* diagc[MCL] = {};
   double* qcell[MCL][MCL] = {};
   double* F[MCL] = {};
-  double* W[MCL] = {};             // wells (mc_set_well), nullptr when none
+  double* W[MCL] = {};             // wells in effect (mc_set_well), nullptr when none
   double* FW[MCL] = {};
+  double* W_buf[MCL] = {};         // the well buffers, kept across removal / re-adding
+  double* FW_buf[MCL] = {};
   double* p[MCL] = {};
   double* pprev[MCL] = {};
   double* r[MCL] = {};

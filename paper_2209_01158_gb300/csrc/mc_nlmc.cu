@@ -7,8 +7,12 @@
 //     of the coupled fine operator D + Q restricted to K_i^+ (zero Dirichlet
 //     data on the part of the region boundary inside the domain, through a
 //     ghost value at h/2: T = 2 k) subject to Eq. eq:basis's constraints
-//     mean_{K_j}(psi_alpha) = delta_ij delta_alpha,beta for every coarse block
-//     K_j of the region and every alpha.
+//     mean_{K_j^alpha}(psi_alpha) = delta_ij delta_alpha,beta for every coarse
+//     block K_j of the region and every alpha, K_j^alpha = Omega_alpha ∩ K_j:
+//     a continuum given a support mask (an embedded fracture continuum: its
+//     fracture cells) is averaged over its own cells only, and a block
+//     without such cells has no coarse unknown of that continuum (no basis
+//     function, zero rows and columns of A_bar, state 0).
 //     Solver: projected preconditioned CG in the null space of the
 //     constraints. psi = psi0 + w with psi0 the indicator of K_i in continuum
 //     beta; the Jacobi-preconditioned residual is projected by subtracting,
@@ -21,9 +25,15 @@
 //     domain boundary), on the region plus a one-cell ring.
 //   * A_bar = R A R^T: A_bar[(i,alpha),(j,beta)] = sum psi^{i,alpha} . V^{j,beta}
 //     over the overlap, one CTA per pair of blocks that can interact.
-//   * M_bar = diag(c_alpha |K_i|), F_bar = block sums of the fine sources
-//     (the coarse finite-volume forms the paper gives for piecewise-constant
-//     data).
+//   * Optional conservative form: every diagonal entry of A_bar is set to
+//     minus the sum of the other entries of its row, so that A_bar 1 = 0 as
+//     for the exact (globally oversampled) basis; the truncated local basis
+//     breaks this, and with very permeable fractures the defect outweighs
+//     the coarse mass term.
+//   * M_bar = diag(c_alpha |K_i^alpha|), F_bar = block sums of the fine
+//     sources, wells W_bar = sums of W over K_i^alpha with right-hand side the
+//     sums of W p_w (the coarse finite-volume forms the paper gives for
+//     piecewise-constant data).
 // Coarse stepping (Sections 4.2-4.3): coupled (Eq. is-nlmc) or the D-, L-,
 // U-schemes with A0_bar from the diagonal / lower / upper blocks of A_bar.
 // The coarse systems are small and dense: their inverses are formed once by
@@ -57,6 +67,11 @@ struct mc_nlmc {
   double* Abar = nullptr;    // (L Nc)^2, row-major
   double* mbar = nullptr;    // L Nc
   double* fbar = nullptr;    // L Nc
+  double* wbar = nullptr;    // L Nc: coarse well index (sum of W over K_i^alpha)
+  double* wpbar = nullptr;   // L Nc: sum of W p_w over K_i^alpha
+  int* nsup = nullptr;       // L Nc: cells of K_i^alpha (0: no coarse unknown)
+  unsigned char* sup = nullptr;  // L pitched masks of Omega_alpha (continua given one)
+  int flags = 0;
   double* Gd = nullptr;      // L blocks of Nc^2: inverses of M_bar_a/tau + A_bar_aa
   double* Gc = nullptr;      // (L Nc)^2: inverse of M_bar/tau + A_bar
   double* gjrow = nullptr;   // Gauss-Jordan pivot row / column buffers (2 * L Nc)
@@ -106,7 +121,13 @@ struct FineRef {
   const double* k[MCL];
   double qconst[MCL][MCL];
   const double* qcell[MCL][MCL];
+  const unsigned char* sup[MCL];   // pitched mask of Omega_a, or nullptr (every cell)
 };
+
+// Cell gi (pitched index) of continuum a belongs to Omega_a.
+__device__ __forceinline__ bool in_sup(const FineRef& f, int a, long long gi) {
+  return f.sup[a] == nullptr || f.sup[a][gi] != 0;
+}
 
 __device__ __forceinline__ double fq(const FineRef& f, int a, int b, long long gi) {
   return f.qcell[a][b] ? __ldg(f.qcell[a][b] + gi) : f.qconst[a][b];
@@ -121,6 +142,7 @@ struct BasisArgs {
   double rtol;
   int max_iter;
   long long* dits;
+  const int* nsup;   // [L][Nc] cells of K_j^alpha
 };
 
 // A_loc x at local cell (g, ly, lx) of region R (Dirichlet ghosts inside the
@@ -225,22 +247,28 @@ __global__ void __launch_bounds__(BT, 1) nlmc_basis_kernel(const BasisArgs A) {
     const int i = task / L, beta = task - i * L;
     const int I = i % A.ncx, J = i / A.ncx;
     const Region R = region_of(I, J, A.ncx, A.ncy, A.layers, A.bx, A.by);
+    if (A.nsup[beta * Nc + i] == 0) continue;  // K_i^beta empty: no coarse unknown (uniform)
     const int nb = R.nbx * R.nby;
     const int nblk = L * nb;
     const int cblk = beta * nb + R.centre;
     double* w = A.psi + ((size_t)i * L + beta) * A.rsz;
-    // w = p = psi0 (indicator of the centre block in continuum beta); invd and
-    // its block sums
+    auto sup_of = [&](int g, int ly, int lx) -> bool {
+      return in_sup(A.f, g, (long long)(R.y0 + ly) * A.f.pitch + R.x0 + lx);
+    };
+    // w = p = psi0 (indicator of K_i^beta in continuum beta); invd and its
+    // sums over every K_j^alpha (constrained cells only)
     clear_part();
     for_cells(A, R, [&](int g, int ly, int lx, int blk, bool ok) {
       double d = 0.0;
       if (ok) {
         const long long li = idx(g, ly, lx);
-        const double v = blk == cblk ? 1.0 : 0.0;
+        const bool s_in = sup_of(g, ly, lx);
+        const double v = (blk == cblk && s_in) ? 1.0 : 0.0;
         w[li] = v;
         p[li] = v;
-        d = 1.0 / diag_loc(A, R, g, ly, lx);
-        iv[li] = d;
+        const double dv = 1.0 / diag_loc(A, R, g, ly, lx);
+        iv[li] = dv;
+        d = s_in ? dv : 0.0;
       }
       const double s = warp_sum_d(d);
       if (lane == 0) part[warp * MAXBLK + blk] += s;
@@ -254,19 +282,19 @@ __global__ void __launch_bounds__(BT, 1) nlmc_basis_kernel(const BasisArgs A) {
         const long long li = idx(g, ly, lx);
         const double rv = -apply_loc(A, R, p, g, ly, lx);
         r[li] = rv;
-        t = iv[li] * rv;
+        t = sup_of(g, ly, lx) ? iv[li] * rv : 0.0;
       }
       const double s = warp_sum_d(t);
       if (lane == 0) part[warp * MAXBLK + blk] += s;
     });
     block_totals(part, mean, nblk);
-    for (int b = threadIdx.x; b < nblk; b += BT) mean[b] = mean[b] / sinv[b];
+    for (int b = threadIdx.x; b < nblk; b += BT) mean[b] = sinv[b] > 0.0 ? mean[b] / sinv[b] : 0.0;
     __syncthreads();
     double acc[1] = {0.0};
     for_cells(A, R, [&](int g, int ly, int lx, int blk, bool ok) {
       if (!ok) return;
       const long long li = idx(g, ly, lx);
-      const double rv = r[li] - mean[blk];
+      const double rv = r[li] - (sup_of(g, ly, lx) ? mean[blk] : 0.0);
       r[li] = rv;
       const double z = iv[li] * rv;
       p[li] = z;
@@ -298,19 +326,19 @@ __global__ void __launch_bounds__(BT, 1) nlmc_basis_kernel(const BasisArgs A) {
           w[li] += al * p[li];
           const double rv = r[li] - al * q[li];
           r[li] = rv;
-          t = iv[li] * rv;
+          t = sup_of(g, ly, lx) ? iv[li] * rv : 0.0;
         }
         const double s = warp_sum_d(t);
         if (lane == 0) part[warp * MAXBLK + blk] += s;
       });
       block_totals(part, mean, nblk);
-      for (int b = threadIdx.x; b < nblk; b += BT) mean[b] = mean[b] / sinv[b];
+      for (int b = threadIdx.x; b < nblk; b += BT) mean[b] = sinv[b] > 0.0 ? mean[b] / sinv[b] : 0.0;
       __syncthreads();
       double rzn[1] = {0.0};
       for_cells(A, R, [&](int g, int ly, int lx, int blk, bool ok) {
         if (!ok) return;
         const long long li = idx(g, ly, lx);
-        const double rv = r[li] - mean[blk];
+        const double rv = r[li] - (sup_of(g, ly, lx) ? mean[blk] : 0.0);
         r[li] = rv;
         rzn[0] += rv * (iv[li] * rv);
       });
@@ -428,30 +456,79 @@ __global__ void nlmc_galerkin_kernel(const BasisArgs A, const double* V, long lo
   }
 }
 
-// Coarse mass, block sums of F and block means of p.
-__global__ void nlmc_coarse_vectors(const double* const* F, const double* const* p, int L, int nx,
-                                    int pitch, int ncx, int ncy, int bx, int by, double area,
-                                    const double* c, double* mbar, double* fbar, double* pbar) {
+// Cells of K_i^alpha for every block and continuum (one warp each).
+__global__ void nlmc_support_count(FineRef f, int ncx, int ncy, int bx, int by, int* nsup) {
   const int Nc = ncx * ncy;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = warp; t < f.L * Nc; t += nwarps) {
+    const int a = t / Nc, i = t - a * Nc;
+    const int I = i % ncx, J = i / ncx;
+    int cnt = 0;
+    for (int e = lane; e < bx * by; e += 32) {
+      const long long gi = (long long)(J * by + e / bx) * f.pitch + I * bx + e % bx;
+      cnt += in_sup(f, a, gi) ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) nsup[t] = cnt;
+  }
+}
+
+// Coarse mass c |K_i^alpha|, block sums of F, means of p over K_i^alpha, and
+// the coarse well terms (sums of W and W p_w over K_i^alpha); 0 for the
+// unknowns that do not exist.
+__global__ void nlmc_coarse_vectors(FineRef f, const double* const* F, const double* const* p,
+                                    const double* const* W, const double* const* FW, int ncx, int ncy,
+                                    int bx, int by, double area, const double* c, const int* nsup,
+                                    double* mbar, double* fbar, double* pbar, double* wbar,
+                                    double* wpbar) {
+  const int Nc = ncx * ncy;
+  const int L = f.L;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int t = warp; t < L * Nc; t += nwarps) {
     const int a = t / Nc, i = t - a * Nc;
     const int I = i % ncx, J = i / ncx;
-    double sf = 0.0, sp = 0.0;
+    const int ns = nsup[t];
+    double sf = 0.0, sp = 0.0, sw = 0.0, swp = 0.0;
     for (int e = lane; e < bx * by; e += 32) {
-      const long long gi = (long long)(J * by + e / bx) * pitch + I * bx + e % bx;
+      const long long gi = (long long)(J * by + e / bx) * f.pitch + I * bx + e % bx;
       if (F) sf += F[a][gi];
+      if (!in_sup(f, a, gi)) continue;
       if (p) sp += p[a][gi];
+      if (W[a]) {
+        sw += W[a][gi];
+        swp += FW[a][gi];
+      }
     }
     sf = warp_sum_d(sf);
     sp = warp_sum_d(sp);
+    sw = warp_sum_d(sw);
+    swp = warp_sum_d(swp);
     if (lane == 0) {
-      if (mbar) mbar[t] = c[a] * bx * by * area;
-      if (fbar) fbar[t] = sf;
-      if (pbar) pbar[t] = sp / (bx * by);
+      if (mbar) mbar[t] = ns > 0 ? c[a] * ns * area : 0.0;
+      if (fbar) fbar[t] = ns > 0 ? sf : 0.0;
+      if (pbar) pbar[t] = ns > 0 ? sp / ns : 0.0;
+      if (wbar) wbar[t] = ns > 0 ? sw : 0.0;
+      if (wpbar) wpbar[t] = ns > 0 ? swp : 0.0;
     }
+  }
+}
+
+// Conservative form: A_bar[r][r] -= sum of row r (one warp per row; a warp
+// reads only its own row and writes only its diagonal).
+__global__ void nlmc_conserve_kernel(double* Abar, long long n) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long r = warp; r < n; r += nw) {
+    double s = 0.0;
+    for (long long c = lane; c < n; c += 32) s += Abar[r * n + c];
+    s = warp_sum_d(s);
+    if (lane == 0) Abar[r * n + r] -= s;
   }
 }
 
@@ -495,6 +572,8 @@ struct CoarseArgs {
   const double* Abar;
   const double* mbar;
   const double* fbar;
+  const double* wbar;    // coarse well index (diagonal)
+  const double* wpbar;   // coarse well right-hand side
   const double* Gd;
   const double* Gc;
   double* pbar;
@@ -529,7 +608,8 @@ __global__ void nlmc_step_kernel(const CoarseArgs A) {
     for (long long e = gt; e < n; e += gs) A.pprev[e] = __ldcg(A.pbar + e);
     if (!grid_barrier(A.bar)) return;
     if (A.scheme == MC_SCHEME_COUPLED) {
-      for (long long e = gt; e < n; e += gs) A.rhs[e] = A.mbar[e] / A.tau * __ldcg(A.pprev + e) + A.fbar[e];
+      for (long long e = gt; e < n; e += gs)
+        A.rhs[e] = A.mbar[e] / A.tau * __ldcg(A.pprev + e) + A.fbar[e] + A.wpbar[e];
       if (!grid_barrier(A.bar)) return;
       gemv_rows(A.Gc, n, A.rhs, (int)n, A.xt, 0, (int)n, 1.0, false);
       if (!grid_barrier(A.bar)) return;
@@ -537,7 +617,8 @@ __global__ void nlmc_step_kernel(const CoarseArgs A) {
       gemv_rows(A.Abar, n, A.xt, (int)n, A.res, 0, (int)n, 1.0, false);
       if (!grid_barrier(A.bar)) return;
       for (long long e = gt; e < n; e += gs)
-        A.res[e] = __ldcg(A.rhs + e) - A.mbar[e] / A.tau * __ldcg(A.xt + e) - __ldcg(A.res + e);
+        A.res[e] = __ldcg(A.rhs + e) - (A.mbar[e] / A.tau + A.wbar[e]) * __ldcg(A.xt + e) -
+                   __ldcg(A.res + e);
       if (!grid_barrier(A.bar)) return;
       gemv_rows(A.Gc, n, A.res, (int)n, A.xt, 0, (int)n, 1.0, true);
       if (!grid_barrier(A.bar)) return;
@@ -564,7 +645,8 @@ __global__ void nlmc_step_kernel(const CoarseArgs A) {
         for (int a = a0; a < a1; ++a)
           for (long long e = gt; e < Nc; e += gs) {
             const long long r = a * Nc + e;
-            A.rhs[r] = __ldcg(A.rhs + r) + A.mbar[r] / A.tau * __ldcg(A.pprev + r) + A.fbar[r];
+            A.rhs[r] = __ldcg(A.rhs + r) + A.mbar[r] / A.tau * __ldcg(A.pprev + r) + A.fbar[r] +
+                       A.wpbar[r];
           }
         if (!grid_barrier(A.bar)) return;
         for (int a = a0; a < a1; ++a) {
@@ -593,7 +675,7 @@ __global__ void nlmc_step_kernel(const CoarseArgs A) {
               s += __ldcg(A.Abar + row * n + a * Nc + c) * __ldcg(A.xt + a * Nc + c);
             s = warp_sum_d(s);
             if (lane == 0)
-              A.res[row] = __ldcg(A.rhs + row) - A.mbar[row] / A.tau * __ldcg(A.xt + row) - s;
+              A.res[row] = __ldcg(A.rhs + row) - (A.mbar[row] / A.tau + A.wbar[row]) * __ldcg(A.xt + row) - s;
           }
         }
         if (!grid_barrier(A.bar)) return;
@@ -681,24 +763,28 @@ cudaError_t gj_invert(mc_nlmc* m, double* M, int n) {
                                      m->ctx->stream);
 }
 
+// M_bar/tau + W_bar + A_bar restricted to continuum a; a coarse unknown that
+// does not exist (zero mass, zero row and column of A_bar) gets a unit
+// diagonal, so that the inverse exists and maps its zero right-hand side to 0.
 __global__ void copy_block_kernel(const double* Abar, long long n, int a, int Nc, const double* mbar,
-                                  double tau, double* G) {
+                                  const double* wbar, double tau, double* G) {
   const long long tot = (long long)Nc * Nc;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const long long r = e / Nc, c = e - r * Nc;
-    double v = Abar[((long long)a * Nc + r) * n + (long long)a * Nc + c];
-    if (r == c) v += mbar[(long long)a * Nc + r] / tau;
+    const long long ra = (long long)a * Nc + r;
+    double v = Abar[ra * n + (long long)a * Nc + c];
+    if (r == c) v += mbar[ra] > 0.0 ? mbar[ra] / tau + wbar[ra] : 1.0;
     G[e] = v;
   }
 }
 
-__global__ void copy_full_kernel(const double* Abar, long long n, const double* mbar, double tau,
-                                 double* G) {
+__global__ void copy_full_kernel(const double* Abar, long long n, const double* mbar,
+                                 const double* wbar, double tau, double* G) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n * n;
        e += (long long)gridDim.x * blockDim.x) {
     const long long r = e / n, c = e - r * n;
-    G[e] = Abar[e] + (r == c ? mbar[r] / tau : 0.0);
+    G[e] = Abar[e] + (r == c ? (mbar[r] > 0.0 ? mbar[r] / tau + wbar[r] : 1.0) : 0.0);
   }
 }
 
@@ -727,6 +813,12 @@ extern "C" {
 
 mc_status mc_nlmc_build(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
                         double basis_rtol, int32_t basis_max_iter, mc_nlmc** out) {
+  return mc_nlmc_build_ex(ctx, ncx, ncy, layers, basis_rtol, basis_max_iter, nullptr, 0, out);
+}
+
+mc_status mc_nlmc_build_ex(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
+                           double basis_rtol, int32_t basis_max_iter,
+                           const uint8_t* const* support, int32_t flags, mc_nlmc** out) {
   if (!ctx || !out) return MC_E_ARG;
   *out = nullptr;
   if (ncx < 1 || ncy < 1 || layers < 0) return MC_E_ARG;
@@ -735,11 +827,10 @@ mc_status mc_nlmc_build(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
     return MC_E_ARG;
   }
   if (!(basis_rtol > 0.0) || !(basis_rtol < 1.0) || basis_max_iter < 1) return MC_E_ARG;
-  for (int a = 0; a < ctx->L; ++a)
-    if (ctx->W[a]) {
-      ctx->err = "the coarse model takes no wells (mc_set_well)";
-      return MC_E_STATE;
-    }
+  if (flags & ~MC_NLMC_CONSERVATIVE) {
+    ctx->err = "unknown NLMC flags";
+    return MC_E_ARG;
+  }
   const int bx = ctx->nx / ncx, by = ctx->ny / ncy;
   const int span = 2 * layers + 1;
   if ((span < ncx ? span : ncx) * (span < ncy ? span : ncy) * ctx->L > MAXBLK) {
@@ -764,6 +855,7 @@ mc_status mc_nlmc_build(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
   m->tau = ctx->tau;
   m->basis_rtol = basis_rtol;
   m->basis_max_iter = basis_max_iter;
+  m->flags = flags;
   cudaStream_t st = ctx->stream;
   const int L = m->L, Nc = m->Nc;
   const long long n = (long long)L * Nc;
@@ -797,6 +889,9 @@ mc_status mc_nlmc_build(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
   NK(nalloc(m, (void**)&m->gjrow, (size_t)2 * n * sizeof(double)));
   NK(nalloc(m, (void**)&m->mbar, (size_t)n * sizeof(double)));
   NK(nalloc(m, (void**)&m->fbar, (size_t)n * sizeof(double)));
+  NK(nalloc(m, (void**)&m->wbar, (size_t)n * sizeof(double)));
+  NK(nalloc(m, (void**)&m->wpbar, (size_t)n * sizeof(double)));
+  NK(nalloc(m, (void**)&m->nsup, (size_t)n * sizeof(int)));
   NK(nalloc(m, (void**)&m->pbar, (size_t)n * sizeof(double)));
   NK(nalloc(m, (void**)&m->pprev, (size_t)n * sizeof(double)));
   NK(nalloc(m, (void**)&m->rhs, (size_t)n * sizeof(double)));
@@ -811,13 +906,38 @@ mc_status mc_nlmc_build(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
   NK(cudaMemcpyAsync(cdev, ctx->c, MCL * sizeof(double), cudaMemcpyHostToDevice, st));
   const double** Fptr = nullptr;
   const double** Pptr = nullptr;
+  const double** Wptr = nullptr;
+  const double** FWptr = nullptr;
   NK(nalloc(m, (void**)&Fptr, MCL * sizeof(double*)));
   NK(nalloc(m, (void**)&Pptr, MCL * sizeof(double*)));
+  NK(nalloc(m, (void**)&Wptr, MCL * sizeof(double*)));
+  NK(nalloc(m, (void**)&FWptr, MCL * sizeof(double*)));
   NK(cudaMemcpyAsync(Fptr, ctx->F, MCL * sizeof(double*), cudaMemcpyHostToDevice, st));
   NK(cudaMemcpyAsync(Pptr, ctx->p, MCL * sizeof(double*), cudaMemcpyHostToDevice, st));
+  NK(cudaMemcpyAsync(Wptr, ctx->W, MCL * sizeof(double*), cudaMemcpyHostToDevice, st));
+  NK(cudaMemcpyAsync(FWptr, ctx->FW, MCL * sizeof(double*), cudaMemcpyHostToDevice, st));
+  // Omega_alpha masks, pitched like the fine fields (only continua given one)
+  const unsigned char* supd[MCL] = {};
+  int nmask = 0;
+  for (int a = 0; a < L; ++a) nmask += (support && support[a]) ? 1 : 0;
+  if (nmask > 0) {
+    NK(nalloc(m, (void**)&m->sup, (size_t)nmask * ctx->Np));
+    int slot = 0;
+    for (int a = 0; a < L; ++a) {
+      if (!support[a]) continue;
+      unsigned char* dst = m->sup + (size_t)slot++ * ctx->Np;
+      NK(cudaMemcpy2DAsync(dst, ctx->pitch, support[a], ctx->nx, ctx->nx, ctx->ny,
+                           cudaMemcpyHostToDevice, st));
+      supd[a] = dst;
+    }
+  }
 
   BasisArgs A{};
   A.f = fine_ref(ctx, kd);
+  for (int a = 0; a < L; ++a) A.f.sup[a] = supd[a];
+  A.nsup = m->nsup;
+  nlmc_support_count<<<256, 256, 0, st>>>(A.f, ncx, ncy, bx, by, m->nsup);
+  NK(cudaGetLastError());
   A.ncx = ncx;
   A.ncy = ncy;
   A.layers = layers;
@@ -840,16 +960,21 @@ mc_status mc_nlmc_build(mc_ctx* ctx, int32_t ncx, int32_t ncy, int32_t layers,
   nlmc_galerkin_kernel<<<(int)(npair < 65536 ? npair : 65536), 256, 0, st>>>(A, m->V, m->vsz, m->nbr,
                                                                                m->Abar);
   NK(cudaGetLastError());
-  nlmc_coarse_vectors<<<256, 256, 0, st>>>(Fptr, Pptr, L, ctx->nx, ctx->pitch, ncx, ncy, bx, by,
-                                           ctx->h * ctx->h, cdev, m->mbar, m->fbar, m->pbar);
+  if (flags & MC_NLMC_CONSERVATIVE) {
+    nlmc_conserve_kernel<<<(int)((n + 7) / 8), 256, 0, st>>>(m->Abar, n);
+    NK(cudaGetLastError());
+  }
+  nlmc_coarse_vectors<<<256, 256, 0, st>>>(A.f, Fptr, Pptr, Wptr, FWptr, ncx, ncy, bx, by,
+                                           ctx->h * ctx->h, cdev, m->nsup, m->mbar, m->fbar,
+                                           m->pbar, m->wbar, m->wpbar);
   NK(cudaGetLastError());
   for (int a = 0; a < L; ++a) {
-    copy_block_kernel<<<1024, 256, 0, st>>>(m->Abar, n, a, Nc, m->mbar, m->tau,
+    copy_block_kernel<<<1024, 256, 0, st>>>(m->Abar, n, a, Nc, m->mbar, m->wbar, m->tau,
                                             m->Gd + (long long)a * Nc * Nc);
     NK(cudaGetLastError());
     NK(gj_invert(m, m->Gd + (long long)a * Nc * Nc, Nc));
   }
-  copy_full_kernel<<<1024, 256, 0, st>>>(m->Abar, n, m->mbar, m->tau, m->Gc);
+  copy_full_kernel<<<1024, 256, 0, st>>>(m->Abar, n, m->mbar, m->wbar, m->tau, m->Gc);
   NK(cudaGetLastError());
   NK(gj_invert(m, m->Gc, (int)n));
   long long its[4] = {0, 0, 0, 0};
@@ -881,6 +1006,18 @@ mc_status mc_nlmc_info(const mc_nlmc* m, int64_t* info) {
   info[2] = its[0];
   info[3] = its[1];
   info[4] = m->bytes;
+  return MC_OK;
+}
+
+mc_status mc_nlmc_active(mc_nlmc* m, uint8_t* active) {
+  if (!m || !active) return MC_E_ARG;
+  const size_t n = (size_t)m->L * m->Nc;
+  std::vector<int> ns(n);
+  if (cudaMemcpyAsync(ns.data(), m->nsup, n * sizeof(int), cudaMemcpyDeviceToHost, m->ctx->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(m->ctx->stream) != cudaSuccess)
+    return MC_E_CUDA;
+  for (size_t i = 0; i < n; ++i) active[i] = ns[i] > 0 ? 1 : 0;
   return MC_OK;
 }
 
@@ -957,6 +1094,8 @@ mc_status mc_nlmc_step(mc_nlmc* m, int32_t scheme, int32_t nsteps, mc_stats* sta
   A.Abar = m->Abar;
   A.mbar = m->mbar;
   A.fbar = m->fbar;
+  A.wbar = m->wbar;
+  A.wpbar = m->wpbar;
   A.Gd = m->Gd;
   A.Gc = m->Gc;
   A.pbar = m->pbar;

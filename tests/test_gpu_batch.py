@@ -216,3 +216,30 @@ def test_batch_rejects_fp64(mc):
     with pytest.raises(mc.MCError):
         mc.Batch([ctx], opts(mc, precision=0))
     ctx.close()
+
+
+def test_batch_full_size_instances_unforced_hand_over(mc):
+    """Instances of the batched recipe at its two largest sizes (seed 4002:
+    512^2, seed 4015: 1024^2, both two continua) in the benchmark's
+    configuration (rtol 1e-12, ir_max 12): an instance whose FP32 refinement
+    cannot meet the tolerance on its own is handed to the FP64 path with no
+    forcing, and both instances must still match the oracle."""
+    ws_big = [mi.fracture_instance(4002), mi.fracture_instance(4015)]
+    assert [(w.nx, w.L) for w in ws_big] == [(512, 2), (1024, 2)]
+    refs = oracle_runs(ws_big, 1, "D")
+    o = opts(mc, ir_max=12)
+    ctxs = [mc.Context.from_workload(w, opts=o) for w in ws_big]
+    b = mc.Batch(ctxs, o)
+    st = b.step("D", 1)
+    assert st["steps_done"] == 1 and st["status"] == 0, st
+    info = b.info()
+    for i, (c, ref) in enumerate(zip(ctxs, refs)):
+        p = c.get_state()
+        err = metrics.rel_l2(ref, p)
+        mx = max(float(np.max(np.abs(np.ravel(r) - np.ravel(x)))) for r, x in zip(ref, p)) / \
+            max(float(np.max(np.abs(np.ravel(r)))) for r in ref)
+        assert err <= MIXED_TOL and mx <= MIXED_TOL, (i, err, mx, b.instance_stats(i), info)
+    print("fp64_instances", info["fp64_instances"])
+    b.close()
+    for c in ctxs:
+        c.close()

@@ -96,7 +96,7 @@ def test_remove_wells_and_change_precision(mc):
     ctx.close()
 
 
-def test_well_arguments_and_coarse_model_refused(mc):
+def test_well_arguments(mc):
     w = mi.paper_wells(2, n=32)
     ctx = mc.Context.from_workload(w)
     W, pw = w.wells[1]
@@ -106,7 +106,21 @@ def test_well_arguments_and_coarse_model_refused(mc):
         ctx.set_well(1, bad, pw)
     with pytest.raises(mc.MCError):
         ctx.set_well(2, W, pw)
-    with pytest.raises(mc.MCError) as e:
-        mc.NLMC(ctx, 4, 4, 1)
-    assert e.value.status == mc.N.MC_E_STATE
+    ctx.close()
+
+
+def test_well_toggle_reuses_buffers(mc):
+    """Removing and re-adding a well reuses the context's well buffers, and
+    the re-enabled well acts as before."""
+    w = mi.paper_wells(2, n=32)
+    ctx = mc.Context.from_workload(w)
+    W, pw = w.wells[1]
+    b0 = ctx.device_bytes()
+    for _ in range(3):
+        ctx.set_well(1, None, None)
+        ctx.set_well(1, W, pw)
+    assert ctx.device_bytes() == b0
+    ctx.step("D", 3)
+    ref = from_workload(w).run(w.p0, w.F, 3, "D")
+    assert metrics.rel_l2(ref, ctx.get_state()) <= 1e-10
     ctx.close()
