@@ -119,18 +119,24 @@ def reduce_max(x, ws, device):
     return float(t.item())
 
 
-def peaks():
-    """(HBM GB/s, FP64 TFLOP/s, source). FP64: 2 FMA lanes per SM per clock
-    (ncu's derived peak on GB300) x 152 SMs x 2 FLOP x the max SM clock."""
+def peaks(mc, torch, stream):
+    """HBM GB/s (MEASURED_PEAKS.json, else the fallback), and the FP64 rate:
+    measured live by the library's DFMA-throughput kernel (mc_fp64_fma_rate,
+    CUDA events, median of 5), with the unit-count figure (2 FMA lanes per SM
+    and clock x SMs x 2 FLOP x max SM clock) beside it."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        hbm = float(d["hbm_gbs"])
+        hbm, hbm_kind = float(d["hbm_gbs"]), "measured"
         mhz = float(d.get("sm_max_mhz", 2070.0))
-        return hbm, 2 * 152 * 2 * mhz * 1e6 / 1e12, "measured"
     except Exception:
-        return 6800.0, 2 * 152 * 2 * 2070e6 / 1e12, "fallback"
+        hbm, hbm_kind, mhz = 6800.0, "fallback", 2070.0
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    rates = sorted(mc.mc_fp64_fma_rate(stream) for _ in range(5))
+    return {"hbm": hbm, "hbm_kind": hbm_kind, "fp64": rates[2],
+            "fp64_kind": "measured (DFMA-throughput kernel, median of 5)",
+            "fp64_units": 2 * sms * 2 * mhz * 1e6 / 1e12, "sms": sms}
 
 
 def crop(w, m):
@@ -371,6 +377,123 @@ def batched_extra(args, mc, mi, torch, stream, ws, precond=0):
             "max_final_rel_residual": relres}
 
 
+def support_means(fields, sup, nc):
+    """Means of each fine field over the cells of K_j^alpha (the coarse
+    unknowns of the NLMC model); `sup` as given to mc.NLMC."""
+    out = []
+    for a, x in enumerate(fields):
+        n = int(round(np.sqrt(np.size(x))))
+        bs = n // nc
+        m = np.ones((n, n), bool) if sup is None or sup[a] is None else np.asarray(sup[a], bool)
+        v = np.where(m, np.asarray(x).reshape(n, n), 0.0).reshape(nc, bs, nc, bs).sum(axis=(1, 3))
+        c = m.reshape(nc, bs, nc, bs).sum(axis=(1, 3))
+        out.append(np.divide(v, c, out=np.zeros_like(v), where=c > 0).ravel())
+    return np.concatenate(out)
+
+
+def nlmc_extra(args, mc, mi, torch, stream, opts_for):
+    """NLMC on the 1024^2 fracture workload (32 x 32 coarse blocks, 2 layers):
+    build time, coarse steps/s, and e_H after 5 steps against the GPU fine
+    coupled solve (FP64, rtol 1e-10; the fine path is oracle-checked by the
+    tests), for the plain Galerkin operator with whole-block constraints and
+    for the Omega_f ∩ K_j constraints with the conservative operator."""
+    wn = mi.nlmc_1024(n=args.n)
+    cn = mc.Context.from_workload(wn, opts=opts_for(1e-10), stream=stream)
+    cn.step("coupled", 5)
+    fine = cn.get_state()
+    cn.set_state(wn.p0)
+    out = {"workload": "nlmc_1024 (fracture recipe 1024^2, L=2, 32x32 blocks, 2 layers, tau=1/200, "
+                       "p0=0, point sources)"}
+    sup_f = [None, wn.support[1]]
+    for name, sup, cons in (("plain", None, False), ("support_conservative", sup_f, True)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nl = mc.NLMC(cn, 32, 32, 2, support=sup, conservative=cons)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        info = nl.info()
+        act = nl.active()
+        ref = support_means(fine, sup, 32)
+        r = {"build_s": t_build, "basis_pcg_iterations": info["basis_iters"],
+             "coarse_unknowns": int(act.sum())}
+        for scheme in ("coupled", "D"):
+            nl.set_state(support_means(wn.p0, sup, 32))
+            nl.step(scheme, 5)
+            pb = nl.get_state()
+            r["e_H_5_steps_" + scheme] = float(np.linalg.norm((pb - ref)[act]) / np.linalg.norm(ref[act]))
+        ncs = 200
+        t0 = time.perf_counter()
+        nl.step("D", ncs)
+        torch.cuda.synchronize()
+        r["coarse_steps_per_s"] = ncs / (time.perf_counter() - t0)
+        nl.close()
+        out[name] = r
+    cn.close()
+    return out
+
+
+def nlmc_paper_extra(mc, mi, opts_for):
+    """NLMC on the paper-shaped 2C problem (200^2, p0 = 1, wells, 50 steps to
+    T = 0.002) on a 20 x 20 coarse grid with 2 layers, fracture support and
+    the conservative operator: e_H in % at steps 10, 30, 50 against the fine
+    coupled GPU run (FP64, rtol 1e-12), the paper's Table 3 metric."""
+    w = mi.paper_wells(2)
+    ctx = mc.Context.from_workload(w, opts=opts_for(1e-12))
+    fine = {}
+    for k in range(1, w.nsteps + 1):
+        ctx.step("coupled", 1)
+        if k in (10, 30, 50):
+            fine[k] = ctx.get_state()
+    ctx.set_state(w.p0)
+    sup = [None, w.support[1]]
+    nl = mc.NLMC(ctx, 20, 20, 2, support=sup, conservative=True)
+    act = nl.active()
+    out = {"workload": "paper_wells 2C 200^2, coarse 20x20, 2 layers, Omega_f support, conservative",
+           "coarse_unknowns": int(act.sum())}
+    for scheme in ("coupled", "D", "U"):
+        nl.set_state(support_means(w.p0, sup, 20))
+        e = []
+        for k in range(1, w.nsteps + 1):
+            nl.step(scheme, 1)
+            if k in fine:
+                ref = support_means(fine[k], sup, 20)
+                pb = nl.get_state()
+                e.append(100.0 * float(np.linalg.norm((pb - ref)[act]) / np.linalg.norm(ref[act])))
+        out["e_H_percent_" + scheme] = e
+    nl.close()
+    ctx.close()
+    return out
+
+
+def summary_of(value, roof, e2e, extras):
+    """The key numbers of every line, flat, for the end of the JSON line."""
+    s = {"fp64_D_value": value, "fp64_frac": roof["frac"], "fp64_hbm_frac": roof["hbm_frac"],
+         "e2e": e2e["value"] if e2e else None}
+    g = lambda *ks: _dig(extras, ks)
+    s.update({
+        "coupled_value": g("coupled", "value"), "decoupled_speedup": g("coupled", "decoupled_speedup"),
+        "two_level_value": g("fp64_two_level", "value"),
+        "two_level_speedup_vs_coupled": g("fp64_two_level", "speedup_vs_coupled"),
+        "fp32_ir_value": g("fp32_ir", "value"), "fp32_ir_hbm_frac": g("fp32_ir", "roofline_inner", "frac"),
+        "bf16t_ir_value": g("bf16t_ir", "value"),
+        "p4096_fp32_hbm_frac": g("precision_4096", "fp32", "roofline_inner", "frac"),
+        "p4096_bf16t_hbm_frac": g("precision_4096", "bf16t", "roofline_inner", "frac"),
+        "nlmc_plain_e_H_D": g("nlmc", "plain", "e_H_5_steps_D"),
+        "nlmc_support_e_H_D": g("nlmc", "support_conservative", "e_H_5_steps_D"),
+        "nlmc_paper2c_e_H_pct_D": g("nlmc_paper_2c", "e_H_percent_D"),
+        "batched_value": g("batched", "value"), "batched_fp64_instances": g("batched", "fp64_instances"),
+    })
+    return s
+
+
+def _dig(d, ks):
+    for k in ks:
+        if not isinstance(d, dict) or k not in d:
+            return None
+        d = d[k]
+    return d
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -432,7 +555,8 @@ def main():
         ctx.close()
         return max_over_ranks(sum(per)), its, sweeps
 
-    hbm, fp64_tf, peak_kind = peaks()
+    pk = peaks(mc, torch, stream)
+    hbm, fp64_tf = pk["hbm"], pk["fp64"]
     clocks = Clocks()
     clocks.start()
     dev_time, its, _ = timed_run("D", opts_for(RTOL_D))
@@ -444,10 +568,13 @@ def main():
     roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_tf, "unit": "TFLOP/s",
             "frac": achieved_tf / fp64_tf,
             "traffic": None if tpu is None else tpu * cell_its / args.steps,
-            "peak_kind": "FP64 pipe: 2 DFMA lanes/SM/clock x 152 SMs x max clock (%s)" % peak_kind,
-            "kernel": "step_kernel<3,false> (FP64 D-scheme, one launch per time step)",
+            "peak_kind": "FP64 FMA rate %s; unit-count figure %.3f TFLOP/s (%d SMs x 2 DFMA "
+                         "lanes x max clock)" % (pk["fp64_kind"], pk["fp64_units"], pk["sms"]),
+            "kernel": "step_kernel<3,0,0> (FP64 D-scheme, one launch per time step)",
+            "flop_per_cell_iteration": FLOP_PER_CELL_IT,
+            "hbm_frac": BYTES_PER_CELL_IT * cell_its / dev_time / 1e9 / hbm,
             "hbm_view": {"achieved": BYTES_PER_CELL_IT * cell_its / dev_time / 1e9, "peak": hbm,
-                         "unit": "GB/s",
+                         "unit": "GB/s", "peak_kind": pk["hbm_kind"],
                          "frac": BYTES_PER_CELL_IT * cell_its / dev_time / 1e9 / hbm}}
 
     extras = {}
@@ -508,40 +635,8 @@ def main():
            "h2d_bytes_per_step": 8 * L * Ncell, "d2h_bytes_per_step": 8 * L * Ncell}
 
     if not args.no_extras:
-        # NLMC coarse model on the 1024^2 fracture workload: build, coarse steps
-        wn = mi.nlmc_1024(n=args.n)
-        # the fine coupled reference for e_H (a ~1e-2 quantity) needs rtol 1e-8 only
-        cn = mc.Context.from_workload(wn, opts=opts_for(1e-8), stream=stream)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        nl = mc.NLMC(cn, 32, 32, 2)
-        torch.cuda.synchronize()
-        t_build = time.perf_counter() - t0
-        info = nl.info()
-        ncs = 200
-        t0 = time.perf_counter()
-        nl.step("D", ncs)
-        torch.cuda.synchronize()
-        t_coarse = time.perf_counter() - t0
-        bs = wn.nx // 32
-
-        def coarse_mean(fields):
-            return np.concatenate([np.asarray(x).reshape(32, bs, 32, bs).mean(axis=(1, 3)).ravel()
-                                   for x in fields])
-
-        nl.set_state(coarse_mean(wn.p0))
-        nl.step("D", 5)
-        pbar = nl.get_state()
-        cn.step("coupled", 5)
-        ref = coarse_mean(cn.get_state())
-        e_h = float(np.linalg.norm(pbar - ref) / np.linalg.norm(ref))
-        nl.close()
-        cn.close()
-        extras["nlmc"] = {"workload": "nlmc_1024: fracture field 1024x1024, L=2, 32x32 coarse blocks, "
-                                      "2 oversampling layers, tau=1/200",
-                          "build_s": t_build, "basis_pcg_iterations": info["basis_iters"],
-                          "coarse_steps_per_s": ncs / t_coarse,
-                          "coarse_D_e_H_after_5_steps_vs_fine_coupled": e_h}
+        extras["nlmc"] = nlmc_extra(args, mc, mi, torch, stream, opts_for)
+        extras["nlmc_paper_2c"] = nlmc_paper_extra(mc, mi, opts_for)
 
     if not args.no_extras:
         extras["precision_4096"] = precision_extra(args, mc, mi, torch, stream, ws, hbm)
@@ -580,6 +675,7 @@ def main():
             "clocks": ck,
         }
         line.update(extras)
+        line["summary"] = summary_of(value, roof, e2e, extras)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
