@@ -15,10 +15,11 @@ also takes the paper's initial state, time span and well parameters).
 from .fields import correlated_lognormal, segment_lengths, random_segments
 from .configs import (Workload, dual_64, triple_1024, precision_4096,
                       fracture_instance, batched_instances, nlmc_1024, paper_wells, scaled,
-                      by_name)
+                      by_name, Fracture1D, fracture1d, fracture1d_sources)
 
 __all__ = [
     "correlated_lognormal", "segment_lengths", "random_segments", "Workload",
     "dual_64", "triple_1024", "precision_4096", "fracture_instance", "batched_instances",
-    "nlmc_1024", "paper_wells", "scaled", "by_name",
+    "nlmc_1024", "paper_wells", "scaled", "by_name", "Fracture1D", "fracture1d",
+    "fracture1d_sources",
 ]

@@ -36,6 +36,7 @@ class Workload:
     # implicit wells: continuum -> (W = q_w |cell| per cell, p_w per cell)
     wells: Dict[int, Tuple[np.ndarray, np.ndarray]] = field(default_factory=dict)
     coarse: Optional[Tuple[int, int, int]] = None   # (ncx, ncy, layers)
+    frac: Optional["Fracture1D"] = None             # lower-dimensional fracture continuum
     seed: Optional[int] = None
     # continuum -> boolean (ny, nx) cells where the continuum physically lives
     # (an embedded fracture continuum: the cells its segments cross); absent
@@ -234,6 +235,84 @@ def paper_wells(L=2, n=200, seed=None, nsteps=50, qw=1e5, pw=1.2):
                  [np.zeros((n, n)) for _ in range(L)], [np.ones((n, n)) for _ in range(L)],
                  sigma_cell=sc, seed=seed, support={L - 1: ell > 0.0})
     w.wells = {L - 1: (W, np.full((n, n), pw))}
+    return w
+
+
+@dataclass
+class Fracture1D:
+    """The lower-dimensional fracture continuum of a workload (inputs only):
+    segments (S, 4) as (x0, y0, x1, y1), not clipped; fracture permeability
+    kf and capacity cf of the 1-D mesh; matrix-fracture exchange sigma_f per
+    matrix continuum; point sources (x, y, value) put on the fracture piece
+    nearest to the point; wells q_w (p_w - p) on the pieces whose midpoints
+    lie in the boxes (x0, x1, y0, y1), of index q_w per unit length."""
+    segments: np.ndarray
+    kf: float
+    cf: float
+    sigma_f: np.ndarray
+    sources: List[Tuple[float, float, float]] = field(default_factory=list)
+    well_boxes: List[Tuple[float, float, float, float]] = field(default_factory=list)
+    qw: float = 0.0
+    pw: float = 0.0
+    p0: float = 0.0
+
+
+def fracture1d(L=1, n=200, seed=None, nsteps=50, nseg=(25, 25), tau=None, p0=1.0, wells=True):
+    """Matrix continua on the n x n grid plus a fracture continuum on its own
+    1-D mesh: the shape of the paper's 2C (L = 1 matrix continuum) and 3C
+    (L = 2: matrix and natural fractures) problems (Section 5), with seeded
+    segments (centre U[0,1]^2, length U[0.05, 0.5], angle U[0, pi)) standing
+    in for its 25-line geometry.
+
+    2C: matrix c = 0.1, k = 1; fracture c_f = 1, k_f = 1e6.
+    3C: matrix c = 0.05, k = 1e-3; natural fractures c = 0.1, k = 1
+        (exchange 5 with the matrix); fracture as in 2C.
+    Fracture-matrix exchange sigma_f = 1 for every matrix continuum.
+    p^0 = p0 everywhere; wells q_w = 1e5 per unit length at p_w = 1.2 on the
+    pieces in [0.1, 0.15]^2 and [0.6, 0.65] x [0.85, 0.9] (wells=True);
+    T = 0.002 in `nsteps` steps unless tau is given.
+    """
+    if L not in (1, 2):
+        raise ValueError("L (matrix continua) must be 1 or 2")
+    seed = 7000 + L if seed is None else seed
+    rng = np.random.default_rng(seed)
+    segs = random_segments(rng, nseg[0], nseg[1])
+    if L == 1:
+        k = [np.ones((n, n))]
+        c = np.array([0.1])
+        sigma = np.zeros((1, 1))
+    else:
+        k = [np.full((n, n), 1e-3), np.ones((n, n))]
+        c = np.array([0.05, 0.1])
+        sigma = _sym(2, {(0, 1): 5.0})
+    tau = 0.002 / nsteps if tau is None else tau
+    w = Workload("frac1d_%dC_%d" % (L + 1, n), n, n, L, k, c, sigma, tau, nsteps,
+                 [np.zeros((n, n)) for _ in range(L)], [np.full((n, n), p0) for _ in range(L)],
+                 seed=seed)
+    w.frac = Fracture1D(segs, 1e6, 1.0, np.ones(L),
+                        well_boxes=[(0.1, 0.15, 0.1, 0.15), (0.6, 0.65, 0.85, 0.9)] if wells else [],
+                        qw=1e5 if wells else 0.0, pw=1.2, p0=p0)
+    return w
+
+
+def fracture1d_sources(L=1, n=1024, seed=None, nsteps=10, tau=1.0 / 100):
+    """The 1-D fracture model on the fracture recipe's field (log-normal
+    matrix k, mean 1; for L = 2 natural fractures, mean 1e2) with 20..200
+    seeded segments, p^0 = 0 and point sources +1 / -1 on the pieces nearest
+    to (1/8, 1/8) and (7/8, 7/8); no wells."""
+    seed = 7100 + L if seed is None else seed
+    rng = np.random.default_rng(seed)
+    k = [correlated_lognormal(rng, n, n, 16.0, 1.0)]
+    if L == 2:
+        k.append(correlated_lognormal(rng, n, n, 16.0, 1e2))
+    segs = random_segments(rng)
+    c = np.array([1.0]) if L == 1 else np.array([1.0, 0.2])
+    sigma = np.zeros((1, 1)) if L == 1 else _sym(2, {(0, 1): 5.0})
+    w = Workload("frac1d_src_L%d_%d" % (L, n), n, n, L, k, c, sigma, tau, nsteps,
+                 [np.zeros((n, n)) for _ in range(L)], [np.zeros((n, n)) for _ in range(L)],
+                 seed=seed)
+    w.frac = Fracture1D(segs, 1e4, 0.1, np.full(L, 10.0),
+                        sources=[(0.125, 0.125, 1.0), (0.875, 0.875, -1.0)], p0=0.0)
     return w
 
 
