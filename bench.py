@@ -14,10 +14,11 @@ oracle by the full-size parity test).
 
 Metric: continuum-cell updates per second = L * nx * ny * steps / time. The
 FP64 step kernel is bound by the FP64 pipe on this GPU (2 FP64 FMA lanes per
-SM and clock), so its roofline is the FP64 one (26 FLOP per continuum-cell
-PCG iteration); the HBM view (88 B per continuum-cell iteration) is reported
-beside it, and the FP32 inner kernel of the precision form is reported
-against HBM (44 B per continuum-cell iteration).
+SM and clock), so its roofline is the FP64 one (22 FLOP of algorithmic work
+per continuum-cell Jacobi-PCG iteration, against the FMA rate measured by the
+library's probe kernel); the HBM view (88 B per continuum-cell iteration) is
+reported beside it, and the FP32 inner kernel of the precision form is
+reported against HBM (44 B per continuum-cell iteration).
 
 --impl reference times the FP64 CPU oracle (sparse direct solves) on a
 bounded crop of the same workload instead.
@@ -37,7 +38,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FLOP_PER_CELL_IT = 26.0      # flux-form stencil 13, p.q 2, x/r updates 4, z 1, r.z 2, r.r 2, p 2
+# algorithmic work of one Jacobi-PCG iteration on one continuum-cell, independent
+# of how a kernel evaluates it: 5-point SpMV 9 (5 mul + 4 add), the inner
+# products (p, A p), (r, z), (r, r) 6, the updates of x, r, p 6, z = D^-1 r 1
+FLOP_PER_CELL_IT = 22.0
 BYTES_PER_CELL_IT = 88.0     # 11 FP64 values per continuum-cell PCG iteration
 BYTES_PER_CELL_IT_32 = 44.0  # the same 11 values in FP32
 
@@ -253,33 +257,58 @@ def precision_extra(args, mc, mi, torch, stream, ws, hbm):
     """The precision form on its own workload: two continua on a 4096^2 grid
     (k2 contrast 1e5), FP32 and BF16 transmissibilities in separate runs, FP64
     refinement to rtol 1e-10; one warm-up step, then --precision-steps timed
-    steps (CUDA events on the launch stream). At this size one inner
-    iteration moves ~870 MB, far beyond L2, so the inner kernel's bytes come
-    from HBM."""
+    steps, each timed with CUDA events on the launch stream. At this size one
+    inner iteration moves ~870 MB, far beyond L2, so the inner kernel's bytes
+    come from HBM. After every step (outside the timed region) the state is
+    compared with the FP64 path run for the same steps at rtol 1e-12 (relative
+    L2 over both continua): the per-step error against FP64 that the
+    precision workload asks for; the oracle comparison itself is the test
+    suite's (1024^2 recipe)."""
     w = mi.precision_4096(n=args.precision_n)
     Ncell = w.nx * w.ny
+    nst = 1 + args.precision_steps
     out = {"workload": "precision_4096: 2 continua, %dx%d, k2 = 1e5 exp(0.5 N), tau = 1/50, "
                        "D-scheme, refinement rtol %g" % (w.nx, w.ny, RTOL_D)}
+    o64 = mc.mc_default_opts()
+    o64.rtol = 1e-12
+    c64 = mc.Context.from_workload(w, opts=o64, stream=stream)
+    ref = []
+    for _ in range(nst):
+        c64.step("D", 1)
+        ref.append(c64.get_state())
+    c64.close()
+
+    def rel(a, b):
+        num = sum(float(np.sum((x - y) ** 2)) for x, y in zip(a, b))
+        return (num / sum(float(np.sum(x ** 2)) for x in a)) ** 0.5
+
     for name, prec in (("fp32", 1), ("bf16t", 2)):
         o = mc.mc_default_opts()
         o.precision = prec
         o.rtol = RTOL_D
         ctx = mc.Context.from_workload(w, opts=o, stream=stream)
         ctx.step("D", 1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        st = ctx.step("D", args.precision_steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        dt = e0.elapsed_time(e1) * 1e-3
+        errs = [rel(ref[0], ctx.get_state())]
+        dt, its, sweeps = 0.0, 0.0, 0
+        for k in range(args.precision_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            st = ctx.step("D", 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dt += e0.elapsed_time(e1) * 1e-3
+            its += float(sum(st["iters"][:w.L]))
+            sweeps += st["ir_sweeps"]
+            errs.append(rel(ref[k + 1], ctx.get_state()))
         ctx.close()
-        its = float(sum(st["iters"][:w.L]))
+        st = {"ir_sweeps": sweeps}
         bpc = inner_bytes_per_cell_it(prec, 0)
         gbs = bpc * its * Ncell / dt / 1e9
         out[name] = {"value": ws * w.L * Ncell * args.precision_steps / dt,
                      "unit": "continuum-cell updates/s",
                      "s_per_step": dt / args.precision_steps,
+                     "rel_l2_vs_fp64_per_step": errs,
                      "inner_iterations_per_step": its / args.precision_steps,
                      "ir_sweeps_per_step": st["ir_sweeps"] / args.precision_steps,
                      "roofline_inner": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
@@ -465,6 +494,68 @@ def nlmc_paper_extra(mc, mi, opts_for):
     return out
 
 
+def frac1d_extra(args, mc, mi, torch, stream, opts_for):
+    """The lower-dimensional fracture continuum (its own 1-D mesh):
+    (1) the paper-shaped 2C problem (200^2 matrix, 25 seeded segments split
+        into pieces, k_f = 1e6, p0 = 1, wells, T = 0.002 in 50 steps): time to
+        solution of the whole run per scheme (CUDA events, FP64, rtol 1e-12),
+        PCG iterations per step, and e_h of D/L/U against the coupled run (%);
+    (2) the point-source recipe at 1024^2 (20-200 segments): D-scheme and
+        coupled time per step (2 steps after 1 warm-up) and iterations."""
+    out = {}
+    w = mi.fracture1d(1)
+    ref = None
+    res = {"workload": "frac1d paper-shaped 2C, 200^2, 25 segments, k_f 1e6, 50 steps, FP64 rtol 1e-12"}
+    for scheme in ("coupled", "D", "L", "U"):
+        ctx = mc.Context.from_workload(w, opts=opts_for(1e-12), stream=stream)
+        f = mc.Fracture.from_workload(ctx, w)
+        res["pieces"] = f.P
+        f.step(scheme, 1)
+        f.set_state([np.ravel(x) for x in w.p0], np.full(f.P, w.frac.p0))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st = f.step(scheme, w.nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pm, pf = f.get_state()
+        r = {"s": e0.elapsed_time(e1) * 1e-3,
+             "matrix_iterations_per_step": float(sum(st["iters"][:w.L])) / w.nsteps,
+             "fracture_iterations_per_step": float(st["iters"][w.L]) / w.nsteps}
+        if scheme == "coupled":
+            ref = pm + [pf]
+            r = {"s": r["s"], "iterations_per_step": float(st["iters"][0]) / w.nsteps}
+        else:
+            num = sum(float(np.sum((a - b) ** 2)) for a, b in zip(ref, pm + [pf]))
+            den = sum(float(np.sum(a ** 2)) for a in ref)
+            r["e_h_percent"] = 100.0 * (num / den) ** 0.5
+        res[scheme] = r
+        f.close()
+        ctx.close()
+    res["decoupled_D_speedup"] = res["coupled"]["s"] / res["D"]["s"]
+    out["paper_2c"] = res
+    w = mi.fracture1d_sources(1, n=args.n)
+    big = {"workload": "frac1d point sources, %dx%d, k_f 1e4, tau 1/100, FP64 rtol 1e-10" % (w.nx, w.ny)}
+    for scheme in ("D", "coupled"):
+        ctx = mc.Context.from_workload(w, opts=opts_for(1e-10), stream=stream)
+        f = mc.Fracture.from_workload(ctx, w)
+        big["pieces"] = f.P
+        f.step(scheme, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st = f.step(scheme, 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        big[scheme] = {"s_per_step": e0.elapsed_time(e1) * 1e-3 / 2,
+                       "iterations_per_step": [float(x) / 2 for x in st["iters"][:w.L + 1]]}
+        f.close()
+        ctx.close()
+    big["decoupled_D_speedup"] = big["coupled"]["s_per_step"] / big["D"]["s_per_step"]
+    out["points_1024"] = big
+    return out
+
+
 def summary_of(value, roof, e2e, extras):
     """The key numbers of every line, flat, for the end of the JSON line."""
     s = {"fp64_D_value": value, "fp64_frac": roof["frac"], "fp64_hbm_frac": roof["hbm_frac"],
@@ -472,6 +563,7 @@ def summary_of(value, roof, e2e, extras):
     g = lambda *ks: _dig(extras, ks)
     s.update({
         "coupled_value": g("coupled", "value"), "decoupled_speedup": g("coupled", "decoupled_speedup"),
+        "fp64_single_pass_value": g("fp64_single_pass", "value"),
         "two_level_value": g("fp64_two_level", "value"),
         "two_level_speedup_vs_coupled": g("fp64_two_level", "speedup_vs_coupled"),
         "fp32_ir_value": g("fp32_ir", "value"), "fp32_ir_hbm_frac": g("fp32_ir", "roofline_inner", "frac"),
@@ -481,6 +573,11 @@ def summary_of(value, roof, e2e, extras):
         "nlmc_plain_e_H_D": g("nlmc", "plain", "e_H_5_steps_D"),
         "nlmc_support_e_H_D": g("nlmc", "support_conservative", "e_H_5_steps_D"),
         "nlmc_paper2c_e_H_pct_D": g("nlmc_paper_2c", "e_H_percent_D"),
+        "p4096_fp32_rel_l2_vs_fp64": g("precision_4096", "fp32", "rel_l2_vs_fp64_per_step"),
+        "p4096_bf16t_rel_l2_vs_fp64": g("precision_4096", "bf16t", "rel_l2_vs_fp64_per_step"),
+        "frac1d_2c_D_speedup_vs_coupled": g("frac1d", "paper_2c", "decoupled_D_speedup"),
+        "frac1d_2c_e_h_pct_D": g("frac1d", "paper_2c", "D", "e_h_percent"),
+        "frac1d_1024_D_speedup_vs_coupled": g("frac1d", "points_1024", "decoupled_D_speedup"),
         "batched_value": g("batched", "value"), "batched_fp64_instances": g("batched", "fp64_instances"),
     })
     return s
@@ -528,12 +625,13 @@ def main():
     L, Ncell = w.L, w.nx * w.ny
     cells_steps = L * Ncell * args.steps
 
-    def opts_for(rtol, precision=0, inner_form=0, precond=0):
+    def opts_for(rtol, precision=0, inner_form=0, precond=0, fp64_form=0):
         o = mc.mc_default_opts()
         o.rtol = rtol
         o.precision = precision
         o.inner_form = inner_form
         o.precond = precond
+        o.fp64_form = fp64_form
         return o
 
     def timed_run(scheme, opts):
@@ -570,7 +668,8 @@ def main():
             "traffic": None if tpu is None else tpu * cell_its / args.steps,
             "peak_kind": "FP64 FMA rate %s; unit-count figure %.3f TFLOP/s (%d SMs x 2 DFMA "
                          "lanes x max clock)" % (pk["fp64_kind"], pk["fp64_units"], pk["sms"]),
-            "kernel": "step_kernel<3,0,0> (FP64 D-scheme, one launch per time step)",
+            "kernel": "step_kernel<3,0,2> (FP64 D-scheme, scaled Jacobi PCG, two-pass iteration; "
+                      "one launch per time step)",
             "flop_per_cell_iteration": FLOP_PER_CELL_IT,
             "hbm_frac": BYTES_PER_CELL_IT * cell_its / dev_time / 1e9 / hbm,
             "hbm_view": {"achieved": BYTES_PER_CELL_IT * cell_its / dev_time / 1e9, "peak": hbm,
@@ -584,6 +683,13 @@ def main():
                              "ms_per_step": 1e3 * cdev / args.steps, "rtol": RTOL_COUPLED,
                              "pcg_iterations_per_step": float(np.mean(cits)),
                              "decoupled_speedup": cdev / dev_time}
+        # the same scaled Jacobi PCG with the single-pass (one reduction) iteration
+        rdev, rits, _ = timed_run("D", opts_for(RTOL_D, fp64_form=1))
+        extras["fp64_single_pass"] = {
+            "value": ws * cells_steps / rdev, "unit": "continuum-cell updates/s",
+            "ms_per_step": 1e3 * rdev / args.steps, "rtol": RTOL_D,
+            "pcg_iterations_per_step": float(np.mean(rits)),
+            "speedup_vs_two_pass": dev_time / rdev}
         try:
             tdev, tits, _ = timed_run("D", opts_for(RTOL_D, precond=1))
             tci = float(sum(tits)) * Ncell
@@ -639,6 +745,10 @@ def main():
         extras["nlmc_paper_2c"] = nlmc_paper_extra(mc, mi, opts_for)
 
     if not args.no_extras:
+        try:
+            extras["frac1d"] = frac1d_extra(args, mc, mi, torch, stream, opts_for)
+        except Exception as e:  # report, do not abort the benchmark
+            extras["frac1d"] = {"error": str(e)}
         extras["precision_4096"] = precision_extra(args, mc, mi, torch, stream, ws, hbm)
         extras["paper_wells"] = paper_extra(args, mc, mi, np)
     if not args.no_extras and args.batch > 0:

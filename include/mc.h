@@ -79,6 +79,13 @@ enum { MC_PRECOND_JACOBI = 0, MC_PRECOND_TWO_LEVEL = 1 };
    (Hestenes-Stiefel) recurrences with two. Both are the Jacobi PCG of
    Section 3.3's per-continuum systems in exact arithmetic. */
 enum { MC_INNER_SINGLE_REDUCTION = 0, MC_INNER_TWO_REDUCTIONS = 1 };
+/* Iteration of the FP64 Jacobi PCG (decoupled and coupled schemes). Both run
+   CG on the symmetrically scaled system S^-1 A S^-1, S = diag(sqrt(d)), which
+   is Jacobi PCG on A iterate for iterate. MC_FP64_TWO_PASS: a stencil pass and
+   a pointwise pass per iteration, two grid reductions (textbook recurrences);
+   MC_FP64_SINGLE_PASS: one tile pass and one grid reduction (Chronopoulos-Gear
+   recurrences). */
+enum { MC_FP64_TWO_PASS = 0, MC_FP64_SINGLE_PASS = 1 };
 enum { MC_SCHEME_COUPLED = -1, MC_SCHEME_D = 0, MC_SCHEME_L = 1, MC_SCHEME_U = 2 };
 
 typedef struct {
@@ -103,7 +110,8 @@ typedef struct {
   int32_t blocks;      /* persistent CTAs (0: one per SM x occupancy) */
   int32_t threads;     /* threads per CTA (0: default 512) */
   int32_t inner_form;  /* MC_INNER_* (IR forms; default single reduction) */
-  int32_t reserved;    /* 0 */
+  int32_t fp64_form;   /* MC_FP64_* iteration of the FP64 Jacobi PCG (default
+                          two passes) */
 } mc_opts;
 
 typedef struct {
@@ -431,6 +439,70 @@ mc_status mc_step_single_noalloc(int32_t nx, int32_t ny, const double* k, double
                                  double tau, const double* F, double* p, int32_t nsteps,
                                  double rtol, int32_t max_iter, void* stream,
                                  mc_stats* stats);
+
+/* ---------------- Lower-dimensional fracture continuum ---------------------
+ *
+ * A fracture continuum on its own 1-D mesh, coupled to the context's matrix
+ * continua (Section 2, Eqs. mm-md and mm-tc: the matrix on the square, the
+ * fracture on the segments; Section 3.1, Eqs. app-md and app-tc).
+ *   Mesh: every segment is clipped to the unit square and split at the grid
+ *   lines it crosses and at its crossings with the other segments; each piece
+ *   iota_l (length |iota_l|) is a fracture cell hosted by the matrix cell that
+ *   holds its midpoint. Pieces meeting at a point (a split point, a crossing)
+ *   are coupled pairwise by T_ln = t_l t_n / sum_m t_m, t_l = kf / (|iota_l|/2)
+ *   (two pieces: the two-point value kf / (d_l + d_n)); free segment ends carry
+ *   no flux. Mass cf |iota_l|; exchange with matrix continuum a
+ *   q_al = sigma_f[a] |iota_l| / (h/4) (Eq. app-md: sigma |E| / d with the
+ *   piece as interface and d = h/4).
+ *   Unknowns: the context's L matrix continua (state: mc_get_state) and P
+ *   pieces in segment order, pieces along each segment from its first end.
+ *   Schemes (mc_frac_step): coupled backward Euler over all matrix cells and
+ *   pieces (Eq. ct-mc), or the D-, L-, U-schemes of Section 3.3 with the
+ *   fracture as the last (most permeable) continuum: the matrix continua are
+ *   stepped by the FP64 step kernel with the exchange as an implicit diagonal
+ *   term and a right-hand side from p_f, the fracture by a one-CTA PCG on its
+ *   graph.
+ *
+ * mc_frac_create -- attach a fracture network to ctx (FP64, Jacobi opts;
+ *   nx == ny; L <= MC_MAX_CONTINUA - 1).
+ *   seg      nseg * 4 host doubles (x0, y0, x1, y1) per segment, any extent.
+ *   kf, cf   fracture permeability and capacity (> 0).
+ *   sigma_f  L values >= 0: exchange coefficient with each matrix continuum.
+ *   The matrix wells the context has now are kept (mc_set_well after create
+ *   is not seen). The fracture state and sources start at 0. MC_E_ARG when no
+ *   segment crosses the domain. The context must outlive the object.
+ */
+typedef struct mc_frac mc_frac;
+mc_status mc_frac_create(mc_ctx* ctx, int32_t nseg, const double* seg, double kf, double cf,
+                         const double* sigma_f, mc_frac** out);
+
+/* info[0..4] = pieces P, junctions, graph entries, hosting matrix cells,
+ * device bytes held. */
+mc_status mc_frac_info(const mc_frac* f, int64_t* info);
+
+/* Geometry of the pieces: len (P), mid (2P: x, y), host (P: j*nx + i); any
+ * pointer may be NULL. */
+mc_status mc_frac_pieces(const mc_frac* f, double* len, double* mid, int32_t* host);
+
+/* Cell-integrated fracture sources per piece (P host doubles). */
+mc_status mc_frac_set_source(mc_frac* f, const double* Ff);
+
+/* Implicit fracture wells W (p_w - p) per piece (W >= 0: index x length),
+ * or Wf = NULL to remove them; rebuilds the fracture coefficients. */
+mc_status mc_frac_set_well(mc_frac* f, const double* Wf, const double* pwf);
+
+/* State: pm = L host arrays of nx*ny (or NULL to leave the matrix), pf = P
+ * host doubles (or NULL). */
+mc_status mc_frac_set_state(mc_frac* f, const double* const* pm, const double* pf);
+mc_status mc_frac_get_state(mc_frac* f, double* const* pm, double* pf);
+
+/* nsteps steps of MC_SCHEME_COUPLED / _D / _L / _U. stats: iters[a] and
+ * max_iters[a] for the matrix continua, iters[L] for the fracture (coupled:
+ * iters[0]), rel_residual likewise, steps_done. On failure both the matrix
+ * and the fracture state hold the start of the failed step. */
+mc_status mc_frac_step(mc_frac* f, int32_t scheme, int32_t nsteps, mc_stats* stats);
+
+void mc_frac_destroy(mc_frac* f);
 
 /*
  * mc_fp64_fma_rate -- measurement utility (the paper has no counterpart):

@@ -491,3 +491,110 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Fracture:
+    """Owning wrapper of an mc_frac: a fracture continuum on its own 1-D mesh
+    attached to a Context (which must stay open) holding the matrix continua.
+
+    segments: (S, 4) array of (x0, y0, x1, y1); kf, cf: fracture
+    permeability and capacity; sigma_f: exchange coefficient with each matrix
+    continuum."""
+
+    def __init__(self, ctx, segments, kf, cf, sigma_f):
+        self.ctx = ctx
+        self.L = ctx.L
+        seg = np.ascontiguousarray(np.asarray(segments, dtype=np.float64).reshape(-1, 4))
+        sf = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma_f, dtype=np.float64), (ctx.L,)))
+        h = C.c_void_p()
+        st = _lib().mc_frac_create(ctx.handle, int(seg.shape[0]), seg.ctypes.data_as(N.dp), float(kf),
+                                   float(cf), sf.ctypes.data_as(N.dp), C.byref(h))
+        _check(st, ctx.handle)
+        self._h = h
+        self.P = self.info()["pieces"]
+
+    @classmethod
+    def from_workload(cls, ctx, w):
+        """Attach w.frac to ctx: point sources go to the piece whose midpoint
+        is nearest to the point, wells q_w |piece| to the pieces whose
+        midpoints lie in a well box; the initial fracture state is w.frac.p0."""
+        fr = w.frac
+        f = cls(ctx, fr.segments, fr.kf, fr.cf, fr.sigma_f)
+        ln, mid, _ = f.pieces()
+        if fr.sources:
+            F = np.zeros(f.P)
+            for (x, y, v) in fr.sources:
+                F[int(np.argmin((mid[:, 0] - x) ** 2 + (mid[:, 1] - y) ** 2))] += v
+            f.set_source(F)
+        if fr.well_boxes:
+            W = np.zeros(f.P)
+            for (x0, x1, y0, y1) in fr.well_boxes:
+                inb = ((mid[:, 0] >= x0) & (mid[:, 0] <= x1) & (mid[:, 1] >= y0) & (mid[:, 1] <= y1))
+                W[inb] = fr.qw * ln[inb]
+            f.set_well(W, np.full(f.P, fr.pw))
+        f.set_state(None, np.full(f.P, fr.p0))
+        return f
+
+    def info(self):
+        v = (C.c_int64 * 5)()
+        _check(_lib().mc_frac_info(self._h, v), self.ctx.handle)
+        return {"pieces": v[0], "junctions": v[1], "entries": v[2], "host_cells": v[3],
+                "device_bytes": v[4]}
+
+    def pieces(self):
+        ln = np.empty(self.P)
+        mid = np.empty(2 * self.P)
+        host = np.empty(self.P, dtype=np.int32)
+        _check(_lib().mc_frac_pieces(self._h, ln.ctypes.data_as(N.dp), mid.ctypes.data_as(N.dp),
+                                     host.ctypes.data_as(C.POINTER(C.c_int32))), self.ctx.handle)
+        return ln, mid.reshape(-1, 2), host
+
+    def set_source(self, Ff):
+        p, keep = _dptr(Ff, self.P)
+        _check(_lib().mc_frac_set_source(self._h, p), self.ctx.handle)
+
+    def set_well(self, Wf, pwf):
+        if Wf is None:
+            _check(_lib().mc_frac_set_well(self._h, None, None), self.ctx.handle)
+            return
+        w, kw = _dptr(Wf, self.P)
+        q, kq = _dptr(pwf, self.P)
+        _check(_lib().mc_frac_set_well(self._h, w, q), self.ctx.handle)
+
+    def set_state(self, pm=None, pf=None):
+        arr, keep = (None, None)
+        if pm is not None:
+            arr, keep = _dptr_list([np.ravel(x) if not hasattr(x, "data_ptr") else x for x in pm],
+                                   self.ctx.n)
+        pp, kp = (None, None)
+        if pf is not None:
+            pp, kp = _dptr(pf, self.P)
+        _check(_lib().mc_frac_set_state(self._h, arr, pp), self.ctx.handle)
+
+    def get_state(self):
+        pm = [np.empty(self.ctx.n) for _ in range(self.L)]
+        pf = np.empty(self.P)
+        arr, keep = _dptr_list(pm, self.ctx.n, writable=True)
+        _check(_lib().mc_frac_get_state(self._h, arr, pf.ctypes.data_as(N.dp)), self.ctx.handle)
+        return pm, pf
+
+    def step(self, scheme="D", nsteps=1, check=True):
+        sc = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+        s = N.mc_stats()
+        st = _lib().mc_frac_step(self._h, int(sc), int(nsteps), C.byref(s))
+        d = _stats_dict(s, MC_MAX_CONTINUA)
+        d["return"] = st
+        if check:
+            _check(st, self.ctx.handle)
+        return d
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().mc_frac_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -17,6 +17,7 @@ MC_PRECOND_JACOBI, MC_PRECOND_TWO_LEVEL = 0, 1
 MC_TWO_LEVEL_MAX_TILES = 2048
 MC_INNER_SINGLE_REDUCTION, MC_INNER_TWO_REDUCTIONS = 0, 1
 MC_NLMC_CONSERVATIVE = 1
+MC_FP64_TWO_PASS, MC_FP64_SINGLE_PASS = 0, 1
 MC_SCHEME_COUPLED, MC_SCHEME_D, MC_SCHEME_L, MC_SCHEME_U = -1, 0, 1, 2
 
 dp = C.POINTER(C.c_double)
@@ -32,7 +33,7 @@ class mc_opts(C.Structure):
         ("precision", C.c_int32), ("precond", C.c_int32), ("max_iter", C.c_int32),
         ("ir_max", C.c_int32), ("rtol", C.c_double), ("inner_rtol", C.c_double),
         ("spin_limit", C.c_int64), ("blocks", C.c_int32), ("threads", C.c_int32),
-        ("inner_form", C.c_int32), ("reserved", C.c_int32),
+        ("inner_form", C.c_int32), ("fp64_form", C.c_int32),
     ]
 
 
@@ -90,6 +91,16 @@ SIGNATURES = {
     "mc_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "mc_batch_destroy": (None, [C.c_void_p]),
     "mc_fp64_fma_rate": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mc_frac_create": (C.c_int, [C.c_void_p, C.c_int32, dp, C.c_double, C.c_double, dp,
+                                 C.POINTER(C.c_void_p)]),
+    "mc_frac_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "mc_frac_pieces": (C.c_int, [C.c_void_p, dp, dp, C.POINTER(C.c_int32)]),
+    "mc_frac_set_source": (C.c_int, [C.c_void_p, dp]),
+    "mc_frac_set_well": (C.c_int, [C.c_void_p, dp, dp]),
+    "mc_frac_set_state": (C.c_int, [C.c_void_p, dpp, dp]),
+    "mc_frac_get_state": (C.c_int, [C.c_void_p, dpp, dp]),
+    "mc_frac_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(mc_stats)]),
+    "mc_frac_destroy": (None, [C.c_void_p]),
     "mc_destroy": (None, [C.c_void_p]),
     "mc_last_error": (C.c_char_p, [C.c_void_p]),
     "mc_status_string": (C.c_char_p, [C.c_int]),

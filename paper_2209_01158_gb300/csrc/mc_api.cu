@@ -89,6 +89,10 @@ mc_status check_opts(const mc_opts* o, std::string* why) {
     *why = "inner_form";
     return MC_E_ARG;
   }
+  if (o->fp64_form != MC_FP64_TWO_PASS && o->fp64_form != MC_FP64_SINGLE_PASS) {
+    *why = "fp64_form";
+    return MC_E_ARG;
+  }
   return MC_OK;
 }
 
@@ -146,6 +150,13 @@ void mc_fill_params(const mc_ctx* ctx, StepParams* sp, int scheme, int nsteps) {
     sp->TE[a] = ctx->TE[a];
     sp->TN[a] = ctx->TN[a];
     sp->invd[a] = ctx->invd[a];
+    sp->sqd[a] = ctx->sqd[a];
+    sp->tE[a] = ctx->tE[a];
+    sp->tN[a] = ctx->tN[a];
+    for (int b = 0; b < ctx->L; ++b) sp->qs[a][b] = ctx->qs[a][b];
+    sp->w[0][a] = ctx->w64[0][a];
+    sp->w[1][a] = ctx->w64[1][a];
+    sp->pd[a] = ctx->pd[a];
     sp->F[a] = ctx->F[a];
     sp->W[a] = ctx->W[a];
     sp->FW[a] = ctx->FW[a];
@@ -167,6 +178,11 @@ void mc_fill_params(const mc_ctx* ctx, StepParams* sp, int scheme, int nsteps) {
   sp->relres = ctx->drelres;
   sp->mass_defect = ctx->dmass;
   sp->spin_limit = ctx->opts.spin_limit;
+  sp->single_pass = ctx->opts.fp64_form == MC_FP64_SINGLE_PASS ? 1 : 0;
+}
+
+cudaError_t mc_launch_steps_default(mc_ctx* ctx, const StepParams& sp) {
+  return mc_launch_steps(ctx, sp, launch_blocks(ctx), launch_threads(ctx));
 }
 
 extern "C" {
@@ -296,6 +312,12 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
     CKS(mc_alloc(ctx, (void**)&ctx->TE[a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->TN[a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->invd[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->sqd[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->tE[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->tN[a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->w64[0][a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->w64[1][a], fb));
+    CKS(mc_alloc(ctx, (void**)&ctx->pd[a], fb));
     if (percell) CKS(mc_alloc(ctx, (void**)&ctx->diagc[a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->F[a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->p[a], fb));
@@ -306,6 +328,11 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
     CKS(mc_alloc(ctx, (void**)&ctx->P[1][a], fb));
     CKS(mc_alloc(ctx, (void**)&ctx->q[a], fb));
   }
+  for (int a = 0; a < L; ++a)
+    for (int b = a + 1; b < L; ++b) {
+      CKS(mc_alloc(ctx, (void**)&ctx->qs[a][b], fb));
+      ctx->qs[b][a] = ctx->qs[a][b];
+    }
   const int maxb = mc_step_max_blocks(L, 512, ctx->num_sms);
   if (maxb < 1) {
     cuda_err(ctx, "occupancy query", cudaGetLastError());
@@ -328,6 +355,7 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
     CKS(mc_launch_setup(ctx, a, ctx->k[a]));
   }
   for (int a = 0; a < L; ++a) CKS(mc_launch_diag(ctx, a));
+  CKS(mc_launch_pairs(ctx));
   // TMA descriptors of the tiles the stencil phase stages in shared memory.
   for (int a = 0; a < L; ++a) {
     const int bx = mc_step_box_x(), by = mc_step_box_y();
@@ -341,6 +369,11 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
                       ctx->ny, ctx->pitch, bx, by));
     CKS(mc_encode_map(&ctx->maps.invd[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, ctx->invd[a], ctx->nx,
                       ctx->ny, ctx->pitch, bx, by));
+    CKS(mc_encode_map(&ctx->maps.q[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, ctx->q[a], ctx->nx, ctx->ny,
+                      ctx->pitch, bx, by));
+    for (int k = 0; k < 2; ++k)
+      CKS(mc_encode_map(&ctx->maps.w[k][a], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, ctx->w64[k][a], ctx->nx,
+                        ctx->ny, ctx->pitch, bx, by));
   }
   CKS(cudaStreamSynchronize(ctx->stream));
 #undef CKS
@@ -405,6 +438,7 @@ mc_status mc_set_well(mc_ctx* ctx, int32_t alpha, const double* W, const double*
     ctx->FW[alpha] = nullptr;
   }
   CK(mc_launch_diag(ctx, alpha));
+  CK(mc_launch_pairs(ctx));
   ctx->lo_kind = 0;  // FP32 / BF16 copies of diag and invd are stale
   ctx->tl_ready = 0;  // so is the two-level coarse operator
   CK(cudaStreamSynchronize(ctx->stream));

@@ -55,6 +55,18 @@ struct StepParams {
   double* relres;                  // [MCL]
   double* mass_defect;             // [1]
   long long spin_limit;
+  // Jacobi PCG in scaled variables (decoupled FP64 path): sqrt of the
+  // diagonal and the scaled face values T / sqrt(d_i d_j); nullptr: the
+  // unscaled flux-form iteration
+  const double* sqd[MCL];
+  const double* tE[MCL];
+  const double* tN[MCL];
+  const double* qs[MCL][MCL];      // coupled: q_ab / sqrt(d_a d_b) per cell
+  // single-pass form of the scaled iteration: w = A~ r (double-buffered) and
+  // the search direction p; single_pass selects it
+  double* w[2][MCL];
+  double* pd[MCL];
+  int single_pass;
   // two-level preconditioner (decoupled FP64 path; two_level = 0: Jacobi)
   int two_level;
   int nc;                          // coarse unknowns per continuum (stencil tiles)
@@ -146,6 +158,12 @@ struct mc_ctx {
   double* TE[MCL] = {};
   double* TN[MCL] = {};
   double* invd[MCL] = {};
+  double* sqd[MCL] = {};           // sqrt(diag) and scaled faces (FP64 scaled PCG)
+  double* tE[MCL] = {};
+  double* tN[MCL] = {};
+  double* qs[MCL][MCL] = {};       // scaled exchange of each pair (qs[a][b] == qs[b][a])
+  double* w64[2][MCL] = {};        // single-pass FP64 iteration: w buffers, search direction
+  double* pd[MCL] = {};
   double* diagc[MCL] = {};
   double* qcell[MCL][MCL] = {};
   double* F[MCL] = {};
@@ -251,6 +269,17 @@ cudaError_t mc_launch_single_setup(int nx, int ny, int pitch, double h, double c
                                    const double* k, double* TE, double* TN, double* invd,
                                    cudaStream_t stream);
 cudaError_t mc_launch_diag(mc_ctx* ctx, int a);
+// Scaled exchange q_ab / sqrt(d_a d_b) of every pair (after mc_launch_diag of
+// every continuum).
+cudaError_t mc_launch_pairs(mc_ctx* ctx);
+// The same two set-ups into caller-owned arrays, with the diagonal term W
+// (per cell, or nullptr) in place of the context's wells.
+cudaError_t mc_launch_diag_into(const mc_ctx* ctx, int a, const double* W, double* diagc, double* invd,
+                                double* sqd, double* tE, double* tN);
+cudaError_t mc_launch_pairs_into(const mc_ctx* ctx, double* const* sqd, double* const (*qs)[MCL]);
+// Persistent FP64 step kernel with caller-filled StepParams on the context's
+// stream and TMA maps (cooperative launch, default grid).
+cudaError_t mc_launch_steps_default(mc_ctx* ctx, const StepParams& sp);
 // FW = W * pw in place (FW holds pw on entry), pitched arrays.
 cudaError_t mc_launch_well(mc_ctx* ctx, int a);
 cudaError_t mc_launch_apply(mc_ctx* ctx, int scheme, double* const* x,

@@ -54,8 +54,11 @@ constexpr int NBOX = 4;                 // box slots per ring stage (3 used by t
 constexpr int KM = MC_KMAX_ALLOC;
 
 __device__ __forceinline__ float tload(const float* p, long long i) { return __ldg(p + i); }
+// BF16 transmissibilities through the read-only path: the 16-bit pattern is
+// loaded with ld.global.nc and widened to FP32 (exact).
 __device__ __forceinline__ float tload(const __nv_bfloat16* p, long long i) {
-  return __bfloat162float(p[i]);
+  const unsigned short bits = __ldg(reinterpret_cast<const unsigned short*>(p) + i);
+  return __uint_as_float((unsigned)bits << 16);
 }
 
 // The CTAs that cooperate on one solve: the whole grid, or one team of the

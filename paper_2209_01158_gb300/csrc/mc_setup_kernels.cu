@@ -8,7 +8,9 @@
 // transmissibility (zero-flux condition, Eq. mm-bc). Exchange between
 // co-located continua: q_ab,i = sigma_ab,i |cell| = sigma_ab,i h^2.
 // Diagonal of M_a/tau + D_a + sum_b Q_ab (Section 3.3, D-scheme A0 block):
-//   d_i = c_a h^2 / tau + sum_b q_ab,i + sum over the four faces of T.
+//   d_i = c_a h^2 / tau + sum_b q_ab,i + sum over the four faces of T,
+// its inverse (Jacobi), its square root and the scaled face values
+// T_ij / sqrt(d_i d_j) of the unit-diagonal operator the FP64 PCG iterates on.
 
 #include "mc_internal.h"
 
@@ -54,6 +56,7 @@ struct DiagArgs {
   const double* W;  // well index per cell, or nullptr
   double* diagc;  // may be nullptr (constant case)
   double* invd;
+  double* sqd;    // sqrt of the diagonal, or nullptr
 };
 
 __global__ void diag_kernel(DiagArgs g) {
@@ -73,6 +76,37 @@ __global__ void diag_kernel(DiagArgs g) {
     if (gy > 0) t += g.TN[i - g.pitch];
     if (g.diagc) g.diagc[i] = dc;
     g.invd[i] = 1.0 / (dc + t);
+    if (g.sqd) g.sqd[i] = sqrt(dc + t);
+  }
+}
+
+// Symmetrically scaled face transmissibilities of the Jacobi-scaled operator
+// D^-1/2 A D^-1/2 (unit diagonal): t_ij = T_ij / (sqrt(d_i) sqrt(d_j)).
+__global__ void scaled_faces_kernel(int nx, int ny, int pitch, const double* __restrict__ TE,
+                                    const double* __restrict__ TN, const double* __restrict__ sqd,
+                                    double* __restrict__ tE, double* __restrict__ tN) {
+  const long long Np = (long long)ny * pitch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Np;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+    if (gx >= nx) continue;
+    const double sc = sqd[i];
+    tE[i] = gx + 1 < nx ? TE[i] / (sc * sqd[i + 1]) : 0.0;
+    tN[i] = gy + 1 < ny ? TN[i] / (sc * sqd[i + pitch]) : 0.0;
+  }
+}
+
+// Scaled exchange of a pair of co-located continua: q_ab,i / sqrt(d_a,i d_b,i).
+__global__ void pair_scale_kernel(int nx, int ny, int pitch, const double* __restrict__ qcell,
+                                  double qconst, const double* __restrict__ sa,
+                                  const double* __restrict__ sb, double* __restrict__ qs) {
+  const long long Np = (long long)ny * pitch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Np;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+    if (gx >= nx) continue;
+    const double q = qcell ? qcell[i] : qconst;
+    qs[i] = q / (sa[i] * sb[i]);
   }
 }
 
@@ -158,6 +192,12 @@ cudaError_t mc_launch_setup(mc_ctx* ctx, int a, const double* k_dev) {
 }
 
 cudaError_t mc_launch_diag(mc_ctx* ctx, int a) {
+  return mc_launch_diag_into(ctx, a, ctx->W[a], ctx->diagc[a], ctx->invd[a], ctx->sqd[a], ctx->tE[a],
+                             ctx->tN[a]);
+}
+
+cudaError_t mc_launch_diag_into(const mc_ctx* ctx, int a, const double* W, double* diagc, double* invd,
+                                double* sqd, double* tE, double* tN) {
   DiagArgs g{};
   g.nx = ctx->nx;
   g.ny = ctx->ny;
@@ -171,11 +211,31 @@ cudaError_t mc_launch_diag(mc_ctx* ctx, int a) {
   }
   g.TE = ctx->TE[a];
   g.TN = ctx->TN[a];
-  g.W = ctx->W[a];
-  g.diagc = ctx->diagc[a];
-  g.invd = ctx->invd[a];
+  g.W = W;
+  g.diagc = diagc;
+  g.invd = invd;
+  g.sqd = sqd;
   diag_kernel<<<grid_for(ctx->Np), 256, 0, ctx->stream>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !sqd) return e;
+  scaled_faces_kernel<<<grid_for(ctx->Np), 256, 0, ctx->stream>>>(
+      ctx->nx, ctx->ny, ctx->pitch, ctx->TE[a], ctx->TN[a], sqd, tE, tN);
   return cudaGetLastError();
+}
+
+cudaError_t mc_launch_pairs(mc_ctx* ctx) { return mc_launch_pairs_into(ctx, ctx->sqd, ctx->qs); }
+
+cudaError_t mc_launch_pairs_into(const mc_ctx* ctx, double* const* sqd, double* const (*qs)[MCL]) {
+  for (int a = 0; a < ctx->L; ++a)
+    for (int b = a + 1; b < ctx->L; ++b) {
+      if (!qs[a][b] || !sqd[a] || !sqd[b]) continue;
+      pair_scale_kernel<<<grid_for(ctx->Np), 256, 0, ctx->stream>>>(
+          ctx->nx, ctx->ny, ctx->pitch, ctx->qcell[a][b], ctx->sigma[a][b] * ctx->h * ctx->h,
+          sqd[a], sqd[b], qs[a][b]);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
 }
 
 namespace {

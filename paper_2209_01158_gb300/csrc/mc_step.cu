@@ -20,6 +20,11 @@
 //     66 x 18 halo region, then q = A P_new on the tile and <P_new, q>.
 //   B (pointwise, vectorised): x += alpha P_new, r -= alpha q, z = invd r
 //     (stored for the next phase A), <r, r>, <r, z>.
+// Decoupled Jacobi solves run the same two phases in scaled variables
+// (pcg_solve_scaled): with S = diag(sqrt(d)), Jacobi PCG on A is plain CG on
+// S^-1 A S^-1, whose diagonal is 1 and whose face entries are
+// T_ij / sqrt(d_i d_j), so the stencil costs 4 FMA and 1 add per cell and
+// z = r needs no multiply, no invd read and no z store.
 // Cross-CTA data written inside the launch is read through L2 (ld.cg or TMA,
 // after a proxy fence); read-only coefficients use the read-only path.
 // Reductions are deterministic: warp butterflies, then fixed-order sums over
@@ -808,12 +813,847 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
   return ok;
 }
 
-template <int L, bool COUPLED, bool TLV>
+// ---------------------------------------------------------------------------
+// Jacobi PCG in scaled variables. With S = diag(sqrt(d)) (d the diagonal of
+// the system matrix A: a continuum's block for the decoupled schemes, the
+// whole coupled matrix for the coupled one -- the same d), Jacobi-
+// preconditioned CG on A x = b is, iterate for iterate, plain CG on
+// (S^-1 A S^-1) y = S^-1 b with y = S x: the scaled residual r~ = S^-1 r
+// satisfies r~.r~ = r.(D^-1 r), and the scaled search direction is p~ = S p.
+// The scaled operator has a unit diagonal, face entries
+// t_ij = T_ij / sqrt(d_i d_j) and (coupled) exchange entries
+// q_ab,i / sqrt(d_a,i d_b,i) (set-up kernels), so
+//   q~_a = p~_a - sum_faces t p~_a(neighbour) [- sum_b qs_ab p~_b (coupled)].
+// The stopping test stays the unscaled one, ||b - A x||_2 = ||S r~||_2 <=
+// rtol ||b||_2, evaluated every CHK-th iteration (at most CHK - 1 extra
+// iterations). The initial residual (fused with the right-hand side) and the
+// constant-mode correction after the solve use the unscaled flux form, as in
+// pcg_solve. y lives in the z buffer during the solve; p keeps the unscaled
+// x until the end.
+// The three stages are separate (not inlined) functions so that the
+// iteration loop gets a register allocation of its own.
+constexpr int CHK = 4;
+
+template <int L, bool C>
+__device__ __noinline__ bool scaled_init(const StepParams& sp, unsigned mask, Smem& sm, bool sp1) {
+  const int nx = sp.nx, pitch = sp.pitch;
+  const long long Np = sp.Np;
+  const int tid = threadIdx.x;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
+  const long long gstride = (long long)gridDim.x * blockDim.x;
+  // ---- fused right-hand side + initial residual (slot 0: bb, rr, rz) -----
+  double acc[3 * L];
+#pragma unroll
+  for (int k = 0; k < 3 * L; ++k) acc[k] = 0.0;
+#pragma unroll
+  for (int a = 0; a < L; ++a) {
+    if (!(mask & (1u << a))) continue;
+    const double* pa = sp.p[a];
+    for (long long i = gtid; i < Np; i += gstride) {
+      const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+      if (gx >= nx) continue;
+      const double xc = ldc(pa + i);
+      double f = ldr(sp.F[a] + i);
+      double wx = 0.0;
+      if (sp.W[a]) {
+        f += ldr(sp.FW[a] + i);
+        wx = ldr(sp.W[a] + i) * xc;
+      }
+      double ex = 0.0, exb = 0.0;
+#pragma unroll
+      for (int b = 0; b < L; ++b) {
+        if (b == a) continue;
+        const double qv = qab(sp, a, b, i);
+        const double pb = ldc(sp.p[b] + i);
+        ex += qv * (pb - xc);
+        exb += qv * pb;
+      }
+      const double rv = (f - wx) + ex - stencil_flux(sp, a, pa, gx, gy, i, xc);
+      const double bv = C ? sp.mtau[a] * xc + f : sp.mtau[a] * xc + f + exb;
+      const double s = ldr(sp.sqd[a] + i);
+      const double rt = rv / s;
+      sp.r[a][i] = rt;
+      sp.z[a][i] = xc * s;
+      sp.P[0][a][i] = rt;  // P_old of the first iteration (beta = 0): any finite value
+      if (sp1) {           // single-pass form: s = w = p = 0 before pass -1
+        sp.P[0][a][i] = 0.0;
+        sp.w[0][a][i] = 0.0;
+        sp.pd[a][i] = 0.0;
+      }
+      acc[0 * L + a] += bv * bv;
+      acc[1 * L + a] += rv * rv;
+      acc[2 * L + a] += rt * rt;
+    }
+  }
+  block_store<3 * L>(acc, qbits(mask, L, 3), sm.box, sp.partials, 0);
+  if (!grid_sync(sp)) return false;
+  grid_totals<3 * L>(sp.partials, 0, sm.res);
+  const double rtol2 = sp.rtol * sp.rtol;
+  Scal64& S = *sm.sc;
+  if (tid == 0) {
+    double sb = 0, sr = 0, sz = 0;
+    for (int a = 0; a < L; ++a) {
+      S.bb[a] = sm.res[a];
+      S.rr[a] = sm.res[L + a];
+      S.rz[a] = sm.res[2 * L + a];
+      S.beta[a] = 0.0;
+      S.alpha[a] = 0.0;
+      S.iters[a] = 0;
+      if (mask & (1u << a)) { sb += S.bb[a]; sr += S.rr[a]; sz += S.rz[a]; }
+    }
+    if (C)
+      for (int a = 0; a < L; ++a) { S.bb[a] = sb; S.rr[a] = sr; S.rz[a] = sz; }
+    unsigned act = 0;
+    for (int a = 0; a < L; ++a)
+      if ((mask & (1u << a)) && S.rr[a] > rtol2 * S.bb[a]) act |= 1u << a;
+    S.active = act;
+    S.flag = 0;
+  }
+  __syncthreads();
+  return true;
+}
+
+// The iterations of the scaled solve; slot: next partial-sum slot (in/out).
+template <int L, bool C>
+__device__ __noinline__ bool scaled_loop(const StepParams& sp, const TmaMaps& maps, Smem& sm,
+                                         uint32_t& phb, int& slot_io) {
+  constexpr int NL = C ? L : 1;
+  constexpr int NARR = 2 * NL;
+  constexpr int NST = nstage(L, C);
+  const int nx = sp.nx, ny = sp.ny, pitch = sp.pitch;
+  const long long Np = sp.Np;
+  const int tid = threadIdx.x;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
+  const long long gstride = (long long)gridDim.x * blockDim.x;
+  const double rtol2 = sp.rtol * sp.rtol;
+  Scal64& S = *sm.sc;
+  unsigned active = S.active;
+  int it = 0;
+  int cur = 0;
+  int slot = slot_io;
+  bool ok = true;
+
+  const int tiles = sp.tiles_x * sp.tiles_y;
+  const int lx = tid % TX, ly = tid / TX;  // own cells (lx, ly + RPT * j), j < CPT
+  while (active) {
+    if (it >= sp.max_iter) {
+      if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_NOCONV);
+      ok = false;
+      break;
+    }
+    // ---- phase A: TMA halo tiles of r~ and P_old, P_new = r~ + beta P_old,
+    //      q~ = (S^-1 A S^-1) P_new, <P_new, q~> -------------------------------
+    int act_list[L];
+    int nact = 0;
+#pragma unroll
+    for (int a = 0; a < L; ++a) if (active & (1u << a)) act_list[nact++] = a;
+    double pq[L];
+#pragma unroll
+    for (int a = 0; a < L; ++a) pq[a] = 0.0;
+    const int ntask = C ? tiles : nact * tiles;
+
+    auto issue = [&](int t, int s) {
+      int a0 = 0, tt = t;
+      if (!C) {
+        const int w = t / tiles;
+        tt = t - w * tiles;
+#pragma unroll
+        for (int k = 0; k < L; ++k) if (k == w) a0 = act_list[k];
+      }
+      const int bx0 = (tt % sp.tiles_x) * TX - HOFF;
+      const int by0 = (tt / sp.tiles_x) * TY - 1;
+      uint64_t* bar = sm.bar + s;
+      fence_proxy_async();
+      mbar_expect_tx(bar, NARR * BOX_BYTES);
+      double* base = sm.box + (size_t)s * NARR * ABOX;
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        const int a = C ? l : a0;
+        tma_load_2d(base + (2 * l + 0) * ABOX, &maps.r[a], bx0, by0, bar);
+        tma_load_2d(base + (2 * l + 1) * ABOX, &maps.P[cur][a], bx0, by0, bar);
+      }
+    };
+
+    const int G = gridDim.x;
+    int t = blockIdx.x;
+    int k = 0;
+    unsigned pend = 0;
+#pragma unroll
+    for (int j = 0; j < NST - 1; ++j) {
+      const int tj = t + j * G;
+      if (tj < ntask) {
+        if (tid == 0) issue(tj, j);
+        pend |= 1u << j;
+      }
+    }
+    bool tma_ok = true;
+    for (; t < ntask; t += G, ++k) {
+      const int s = k % NST;
+      {
+        const int tn = t + (NST - 1) * G;
+        const int sn = (k + NST - 1) % NST;
+        if (tn < ntask) {
+          if (tid == 0) issue(tn, sn);
+          pend |= 1u << sn;
+        }
+      }
+      int a0 = 0, tt = t;
+      if (!C) {
+        const int w = t / tiles;
+        tt = t - w * tiles;
+#pragma unroll
+        for (int kk = 0; kk < L; ++kk) if (kk == w) a0 = act_list[kk];
+      }
+      const int x0 = (tt % sp.tiles_x) * TX;
+      const int y0 = (tt / sp.tiles_x) * TY;
+      const int gx = x0 + lx;
+      // scaled face values of the own cells, fetched while TMA lands
+      // (decoupled tiles; the coupled tile loads them in the compute loop)
+      double te[CPT], tw[CPT], tn[CPT], ts[CPT];
+      if (!C) {
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          const int gy = y0 + ly + RPT * j;
+          const long long i = (long long)gy * pitch + gx;
+          te[j] = tw[j] = tn[j] = ts[j] = 0.0;
+          if (gx < nx && gy < ny) {
+            te[j] = ldr(sp.tE[a0] + i);
+            tn[j] = ldr(sp.tN[a0] + i);
+            if (gx > 0) tw[j] = ldr(sp.tE[a0] + i - 1);
+            if (gy > 0) ts[j] = ldr(sp.tN[a0] + i - pitch);
+          }
+        }
+      }
+      if (!mbar_wait(sm.bar + s, (phb >> s) & 1u, sp.spin_limit)) {
+        if (tid == 0) raise_abort(sp, (int)MC_E_TIMEOUT);
+        tma_ok = false;
+        break;
+      }
+      phb ^= 1u << s;
+      pend &= ~(1u << s);
+      const double* base = sm.box + (size_t)s * NARR * ABOX;
+      // decoupled tiles alternate between two P_new areas, so that no CTA
+      // barrier is needed after the stencil (a thread can write area k % 2
+      // only after every thread passed this tile's barrier below, i.e.
+      // finished reading area k % 2 two tiles back)
+      double* pnb = sm.pn + (C ? 0 : (k & 1) * PN);
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        const int a = C ? l : a0;
+        const double bt = S.beta[a];
+        const double* br = base + (2 * l + 0) * ABOX;
+        const double* bp = base + (2 * l + 1) * ABOX;
+        double* pn = pnb + l * PN;
+        for (int e = tid; e < PN; e += NT) {
+          const int ry = e / PX, rx = e - ry * PX;
+          const int bidx = ry * BX + rx + 1;
+          pn[e] = fma(bt, bp[bidx], br[bidx]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int lyj = ly + RPT * j;
+        const int gy = y0 + lyj;
+        if (gx >= nx || gy >= ny) continue;
+        const long long i = (long long)gy * pitch + gx;
+        const int c = (lyj + 1) * PX + lx + 1;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+          const int a = C ? l : a0;
+          double cte, ctw, ctn, cts;
+          if (C) {
+            cte = ldr(sp.tE[a] + i);
+            ctn = ldr(sp.tN[a] + i);
+            ctw = gx > 0 ? ldr(sp.tE[a] + i - 1) : 0.0;
+            cts = gy > 0 ? ldr(sp.tN[a] + i - pitch) : 0.0;
+          } else {
+            cte = te[j]; ctw = tw[j]; ctn = tn[j]; cts = ts[j];
+          }
+          const double* pn = pnb + l * PN;
+          const double pc = pn[c];
+          double nb = fma(cte, pn[c + 1], fma(ctw, pn[c - 1], fma(ctn, pn[c + PX], cts * pn[c - PX])));
+          if (C) {
+#pragma unroll
+            for (int b = 0; b < L; ++b) {
+              if (b == a) continue;
+              nb = fma(ldr(sp.qs[a][b] + i), pnb[b * PN + c], nb);
+            }
+          }
+          const double qv = pc - nb;
+          sp.P[cur ^ 1][a][i] = pc;
+          sp.q[a][i] = qv;
+#pragma unroll
+          for (int kk = 0; kk < L; ++kk) if (kk == a) pq[kk] = fma(pc, qv, pq[kk]);
+        }
+      }
+      if (C) __syncthreads();
+    }
+    if (!tma_ok) {
+      for (int st = 0; st < NST; ++st)
+        if (pend & (1u << st)) mbar_wait(sm.bar + st, (phb >> st) & 1u, 1LL << 24);
+      ok = false;
+      break;
+    }
+    block_store<L>(pq, active, sm.box, sp.partials, slot);
+    if (!grid_sync(sp)) { ok = false; break; }
+    grid_totals<L>(sp.partials, slot, sm.res);
+    slot ^= 1;
+    if (tid == 0) {
+      double pqs = 0.0;
+      for (int a = 0; a < L; ++a) pqs += sm.res[a];
+      int brk = 0;
+      for (int a = 0; a < L; ++a) {
+        S.alpha[a] = 0.0;
+        if (active & (1u << a)) {
+          const double pqt = C ? pqs : sm.res[a];
+          if (!(pqt > 0.0) || !isfinite(pqt)) brk = 1;
+          else S.alpha[a] = S.rz[a] / pqt;
+        }
+      }
+      S.flag = brk;
+    }
+    __syncthreads();
+    if (S.flag) {
+      if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_BREAKDOWN);
+      ok = false;
+      break;
+    }
+    // ---- phase B: y += alpha P_new, r~ -= alpha q~, (r~, r~); every CHK-th
+    //      iteration also ||S r~||^2 for the stopping test ------------------
+    const bool chk = ((it + 1) % CHK) == 0;
+    double acc2[2 * L];
+#pragma unroll
+    for (int kk = 0; kk < 2 * L; ++kk) acc2[kk] = 0.0;
+    const long long Np2 = Np >> 1;
+#pragma unroll
+    for (int a = 0; a < L; ++a) {
+      if (!(active & (1u << a))) continue;
+      const double al = S.alpha[a];
+      double2* y = reinterpret_cast<double2*>(sp.z[a]);
+      double2* r = reinterpret_cast<double2*>(sp.r[a]);
+      const double2* Pn = reinterpret_cast<const double2*>(sp.P[cur ^ 1][a]);
+      const double2* qq = reinterpret_cast<const double2*>(sp.q[a]);
+      const double2* sq = reinterpret_cast<const double2*>(sp.sqd[a]);
+      if (chk) {
+        for (long long j = gtid; j < Np2; j += gstride) {
+          const double2 rv0 = __ldcg(r + j);
+          const double2 qv = __ldcg(qq + j);
+          const double2 yv = __ldcg(y + j);
+          const double2 pv = __ldcg(Pn + j);
+          const double2 sv = __ldg(sq + j);
+          double2 rv, yn;
+          rv.x = fma(-al, qv.x, rv0.x);
+          rv.y = fma(-al, qv.y, rv0.y);
+          yn.x = fma(al, pv.x, yv.x);
+          yn.y = fma(al, pv.y, yv.y);
+          y[j] = yn;
+          r[j] = rv;
+          acc2[L + a] = fma(rv.x, rv.x, fma(rv.y, rv.y, acc2[L + a]));
+          const double ux = sv.x * rv.x, uy = sv.y * rv.y;
+          acc2[a] = fma(ux, ux, fma(uy, uy, acc2[a]));
+        }
+      } else {
+#pragma unroll 2
+        for (long long j = gtid; j < Np2; j += gstride) {
+          const double2 rv0 = __ldcg(r + j);
+          const double2 qv = __ldcg(qq + j);
+          const double2 yv = __ldcg(y + j);
+          const double2 pv = __ldcg(Pn + j);
+          double2 rv, yn;
+          rv.x = fma(-al, qv.x, rv0.x);
+          rv.y = fma(-al, qv.y, rv0.y);
+          yn.x = fma(al, pv.x, yv.x);
+          yn.y = fma(al, pv.y, yv.y);
+          y[j] = yn;
+          r[j] = rv;
+          acc2[L + a] = fma(rv.x, rv.x, fma(rv.y, rv.y, acc2[L + a]));
+        }
+      }
+    }
+    const unsigned qm = chk ? qbits(active, L, 2) : (active << L);
+    block_store<2 * L>(acc2, qm, sm.box, sp.partials, slot);
+    if (!grid_sync(sp)) { ok = false; break; }
+    grid_totals<2 * L>(sp.partials, slot, sm.res);
+    slot ^= 1;
+    ++it;
+    if (tid == 0) {
+      double s0 = 0, s1 = 0;
+      for (int a = 0; a < L; ++a) { s0 += sm.res[a]; s1 += sm.res[L + a]; }
+      unsigned act = active;
+      int bad = 0;
+      for (int a = 0; a < L; ++a) {
+        if (!(active & (1u << a))) continue;
+        const double rzn = C ? s1 : sm.res[L + a];
+        S.beta[a] = rzn / S.rz[a];
+        S.rz[a] = rzn;
+        S.iters[a] = it;
+        if (!isfinite(rzn)) bad = 1;
+        if (rzn == 0.0) {  // exact solution (tiny grids): converged
+          S.rr[a] = 0.0;
+          act &= ~(1u << a);
+        } else if (chk) {
+          const double rra = C ? s0 : sm.res[a];
+          S.rr[a] = rra;
+          if (!(rra > rtol2 * S.bb[a])) act &= ~(1u << a);
+          if (!isfinite(rra)) bad = 1;
+        }
+      }
+      S.active = act;
+      S.flag = bad;
+    }
+    __syncthreads();
+    active = S.active;
+    if (S.flag) {
+      if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_BREAKDOWN);
+      ok = false;
+      break;
+    }
+    cur ^= 1;
+  }
+  slot_io = slot;
+  return ok;
+}
+
+// Back to x = y / sqrt(d) with the constant-mode correction of pcg_solve:
+// decoupled, per solved continuum c_a = 1^T (b - A x)_a / 1^T diag(A0 - D)_a;
+// coupled, one constant per continuum from the L x L Galerkin system; the
+// sums use the non-diffusive terms only (1^T D = 0).
+template <int L, bool C>
+__device__ __noinline__ bool scaled_finish(const StepParams& sp, unsigned mask, Smem& sm, int slot) {
+  constexpr int NPAIR = L * (L - 1) / 2;
+  constexpr int NQC = C ? 2 * L + NPAIR : 2 * L;
+  const int nx = sp.nx, pitch = sp.pitch;
+  const long long Np = sp.Np;
+  const int tid = threadIdx.x;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
+  const long long gstride = (long long)gridDim.x * blockDim.x;
+  Scal64& S = *sm.sc;
+  bool ok = true;
+  double cs[NQC];
+#pragma unroll
+  for (int kk = 0; kk < NQC; ++kk) cs[kk] = 0.0;
+  const bool lag_prev = sp.scheme == MC_SCHEME_D;
+  for (long long i = gtid; i < Np; i += gstride) {
+    const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+    if (gx >= nx) continue;
+    double xv[L];
+#pragma unroll
+    for (int a = 0; a < L; ++a)
+      xv[a] = (mask & (1u << a)) ? ldc(sp.z[a] + i) / ldr(sp.sqd[a] + i) : 0.0;
+    int pi = 0;
+#pragma unroll
+    for (int a = 0; a < L; ++a) {
+      if (!(mask & (1u << a))) continue;
+      double tv = ldr(sp.F[a] + i) + sp.mtau[a] * (ldc(sp.pprev[a] + i) - xv[a]);
+      if (sp.W[a]) {
+        const double wv = ldr(sp.W[a] + i);
+        tv += ldr(sp.FW[a] + i) - wv * xv[a];
+        if (C) cs[L + NPAIR + a] += wv;
+      }
+#pragma unroll
+      for (int b = 0; b < L; ++b) {
+        if (b == a) continue;
+        const double pb = C ? xv[b] : (lag_prev ? ldc(sp.pprev[b] + i) : ldc(sp.p[b] + i));
+        tv += qab(sp, a, b, i) * (pb - xv[a]);
+      }
+      cs[a] += tv;
+      if (!C) cs[L + a] += diagc(sp, a, i);
+    }
+    if (C) {
+#pragma unroll
+      for (int a = 0; a < L; ++a)
+#pragma unroll
+        for (int b = a + 1; b < L; ++b) cs[L + pi++] += qab(sp, a, b, i);
+    }
+  }
+  block_store<NQC>(cs, (1u << NQC) - 1u, sm.box, sp.partials, slot);
+  if (!grid_sync(sp)) {
+    ok = false;
+  } else {
+    double ct[NQC];
+    grid_sum<NQC>(sp.partials, slot, sm.res, ct);
+    double shift[L];
+    if (C) {
+      // G_aa = N m_a/tau + sum_b Q_ab + W_a, G_ab = -Q_ab (Q, W summed over cells)
+      double G[L][L], c[L];
+#pragma unroll
+      for (int a = 0; a < L; ++a) {
+#pragma unroll
+        for (int b = 0; b < L; ++b) G[a][b] = 0.0;
+        G[a][a] = (double)sp.N * sp.mtau[a] + ct[L + NPAIR + a];
+        c[a] = ct[a];
+      }
+      int pi = 0;
+#pragma unroll
+      for (int a = 0; a < L; ++a)
+#pragma unroll
+        for (int b = a + 1; b < L; ++b) {
+          const double Q = ct[L + pi++];
+          G[a][a] += Q;
+          G[b][b] += Q;
+          G[a][b] -= Q;
+          G[b][a] -= Q;
+        }
+#pragma unroll
+      for (int kk = 0; kk < L; ++kk) {
+#pragma unroll
+        for (int r = kk + 1; r < L; ++r) {
+          const double f = G[r][kk] / G[kk][kk];
+#pragma unroll
+          for (int cc = kk; cc < L; ++cc) G[r][cc] -= f * G[kk][cc];
+          c[r] -= f * c[kk];
+        }
+      }
+#pragma unroll
+      for (int r = L - 1; r >= 0; --r) {
+        double v = c[r];
+#pragma unroll
+        for (int cc = r + 1; cc < L; ++cc) v -= G[r][cc] * shift[cc];
+        shift[r] = v / G[r][r];
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < L; ++a) shift[a] = ct[L + a] > 0.0 ? ct[a] / ct[L + a] : 0.0;
+    }
+#pragma unroll
+    for (int a = 0; a < L; ++a) {
+      if (!(mask & (1u << a))) continue;
+      const double sh = isfinite(shift[a]) ? shift[a] : 0.0;
+      for (long long i = gtid; i < Np; i += gstride) {
+        const int gy = (int)(i / pitch), gx = (int)(i - (long long)gy * pitch);
+        if (gx >= nx) continue;
+        sp.p[a][i] = ldc(sp.z[a] + i) / ldr(sp.sqd[a] + i) + sh;
+      }
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+#pragma unroll
+    for (int a = 0; a < L; ++a) {
+      if (!(mask & (1u << a))) continue;
+      if (C && a != 0) continue;
+      sp.iters[a] += S.iters[a];
+      if (S.iters[a] > sp.max_iters[a]) sp.max_iters[a] = S.iters[a];
+      sp.relres[a] = S.bb[a] > 0 ? sqrt(S.rr[a] / S.bb[a]) : sqrt(S.rr[a]);
+    }
+  }
+  // The next solve's first pass reads p and rewrites partial slot 0: every
+  // CTA must be past this solve's last reads first.
+  if (ok && !grid_sync(sp)) ok = false;
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// Single-pass form of the scaled iteration: the Chronopoulos-Gear recurrences
+// of CG on the unit-diagonal system (u = r there, w = A~ r, s = A~ p carried
+// by recurrence), ONE tile pass and ONE grid reduction per iteration. In exact
+// arithmetic the iterates are those of scaled_loop (plain CG); the two inner
+// products gamma = (r, r) and delta = (w, r) of an iteration are formed after
+// the same pass, and alpha = gamma / (delta - beta gamma / alpha_prev).
+// Pass i, tile by tile with a one-cell halo:
+//   s_i = w_i + beta_i s_{i-1},  r_{i+1} = r_i - alpha_i s_i     (tile + halo)
+//   p_i = r_i + beta_i p_{i-1},  y += alpha_i p_i                 (tile)
+//   w_{i+1} = A~ r_{i+1},  gamma, delta (and every CHK-th pass ||S r||^2)
+// The halo values are recomputed from the previous pass's r, s, w (the same
+// fused multiply-adds as their owner tile, so both copies agree bit for bit).
+// r, s, w are double-buffered (buffer `cur` read through TMA, `cur ^ 1`
+// written): r in (r, q), s in (P[0], P[1]), w in (w[0], w[1]); p and y are
+// touched only at their own cells. Pass -1 runs with alpha = beta = 0 on
+// s = w = p = 0 and forms w_0 = A~ r_0 and the first inner products.
+__host__ __device__ constexpr int nstage1(int L, bool coupled) {
+  return !coupled ? 6 : (L <= 1 ? 6 : (L == 2 ? 3 : (L == 3 ? 2 : 1)));
+}
+
+template <int L, bool C>
+__device__ __noinline__ bool sp1_loop(const StepParams& sp, const TmaMaps& maps, Smem& sm, uint32_t& phb,
+                                      int& slot_io) {
+  constexpr int NL = C ? L : 1;
+  constexpr int NARR = 3 * NL;
+  constexpr int NST = nstage1(L, C);
+  const int nx = sp.nx, ny = sp.ny, pitch = sp.pitch;
+  const int tid = threadIdx.x;
+  const double rtol2 = sp.rtol * sp.rtol;
+  Scal64& S = *sm.sc;
+  unsigned active = S.active;
+  int it = -1;
+  int cur = 0;
+  int slot = slot_io;
+  bool ok = true;
+  if (tid == 0)
+    for (int a = 0; a < L; ++a) { S.alpha[a] = 0.0; S.beta[a] = 0.0; }
+  __syncthreads();
+
+  const int tiles = sp.tiles_x * sp.tiles_y;
+  const int lx = tid % TX, ly = tid / TX;
+  while (active) {
+    if (it >= sp.max_iter) {
+      if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_NOCONV);
+      ok = false;
+      break;
+    }
+    const bool chk = it >= 0 && ((it + 1) % CHK) == 0;
+    int act_list[L];
+    int nact = 0;
+#pragma unroll
+    for (int a = 0; a < L; ++a) if (active & (1u << a)) act_list[nact++] = a;
+    double dots[3 * L];   // gamma, delta, ||S r||^2 per continuum
+#pragma unroll
+    for (int a = 0; a < 3 * L; ++a) dots[a] = 0.0;
+    const int ntask = C ? tiles : nact * tiles;
+
+    auto issue = [&](int t, int s) {
+      int a0 = 0, tt = t;
+      if (!C) {
+        const int w = t / tiles;
+        tt = t - w * tiles;
+#pragma unroll
+        for (int k = 0; k < L; ++k) if (k == w) a0 = act_list[k];
+      }
+      const int bx0 = (tt % sp.tiles_x) * TX - HOFF;
+      const int by0 = (tt / sp.tiles_x) * TY - 1;
+      uint64_t* bar = sm.bar + s;
+      fence_proxy_async();
+      mbar_expect_tx(bar, NARR * BOX_BYTES);
+      double* base = sm.box + (size_t)s * NARR * ABOX;
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        const int a = C ? l : a0;
+        tma_load_2d(base + (3 * l + 0) * ABOX, cur ? &maps.q[a] : &maps.r[a], bx0, by0, bar);
+        tma_load_2d(base + (3 * l + 1) * ABOX, &maps.P[cur][a], bx0, by0, bar);
+        tma_load_2d(base + (3 * l + 2) * ABOX, &maps.w[cur][a], bx0, by0, bar);
+      }
+    };
+
+    const int G = gridDim.x;
+    int t = blockIdx.x;
+    int k = 0;
+    unsigned pend = 0;
+#pragma unroll
+    for (int j = 0; j < NST - 1; ++j) {
+      const int tj = t + j * G;
+      if (tj < ntask) {
+        if (tid == 0) issue(tj, j);
+        pend |= 1u << j;
+      }
+    }
+    bool tma_ok = true;
+    for (; t < ntask; t += G, ++k) {
+      const int s = k % NST;
+      {
+        const int tn = t + (NST - 1) * G;
+        const int sn = (k + NST - 1) % NST;
+        if (tn < ntask) {
+          if (tid == 0) issue(tn, sn);
+          pend |= 1u << sn;
+        }
+      }
+      int a0 = 0, tt = t;
+      if (!C) {
+        const int w = t / tiles;
+        tt = t - w * tiles;
+#pragma unroll
+        for (int kk = 0; kk < L; ++kk) if (kk == w) a0 = act_list[kk];
+      }
+      const int x0 = (tt % sp.tiles_x) * TX;
+      const int y0 = (tt / sp.tiles_x) * TY;
+      const int gx = x0 + lx;
+      double te[CPT], tw[CPT], tn[CPT], ts[CPT], pold[CPT], yold[CPT];
+      if (!C) {
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          const int gy = y0 + ly + RPT * j;
+          const long long i = (long long)gy * pitch + gx;
+          te[j] = tw[j] = tn[j] = ts[j] = pold[j] = yold[j] = 0.0;
+          if (gx < nx && gy < ny) {
+            te[j] = ldr(sp.tE[a0] + i);
+            tn[j] = ldr(sp.tN[a0] + i);
+            if (gx > 0) tw[j] = ldr(sp.tE[a0] + i - 1);
+            if (gy > 0) ts[j] = ldr(sp.tN[a0] + i - pitch);
+            pold[j] = ldc(sp.pd[a0] + i);
+            yold[j] = ldc(sp.z[a0] + i);
+          }
+        }
+      }
+      if (!mbar_wait(sm.bar + s, (phb >> s) & 1u, sp.spin_limit)) {
+        if (tid == 0) raise_abort(sp, (int)MC_E_TIMEOUT);
+        tma_ok = false;
+        break;
+      }
+      phb ^= 1u << s;
+      pend &= ~(1u << s);
+      const double* base = sm.box + (size_t)s * NARR * ABOX;
+      // r_{i+1} on the 66 x 18 region of every continuum of the tile
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        const int a = C ? l : a0;
+        const double al = S.alpha[a], bt = S.beta[a];
+        const double* bR = base + (3 * l + 0) * ABOX;
+        const double* bS = base + (3 * l + 1) * ABOX;
+        const double* bW = base + (3 * l + 2) * ABOX;
+        double* pn = sm.pn + l * PN;
+        for (int e = tid; e < PN; e += NT) {
+          const int ry = e / PX, rx = e - ry * PX;
+          const int b = ry * BX + rx + 1;
+          const double sn = fma(bt, bS[b], bW[b]);
+          pn[e] = fma(-al, sn, bR[b]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int lyj = ly + RPT * j;
+        const int gy = y0 + lyj;
+        if (gx >= nx || gy >= ny) continue;
+        const long long i = (long long)gy * pitch + gx;
+        const int c = (lyj + 1) * PX + lx + 1;
+        const int b = (lyj + 1) * BX + lx + HOFF;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+          const int a = C ? l : a0;
+          const double al = S.alpha[a], bt = S.beta[a];
+          const double* bR = base + (3 * l + 0) * ABOX;
+          const double* bS = base + (3 * l + 1) * ABOX;
+          const double* bW = base + (3 * l + 2) * ABOX;
+          double cte, ctw, ctn, cts, po, yo;
+          if (C) {
+            cte = ldr(sp.tE[a] + i);
+            ctn = ldr(sp.tN[a] + i);
+            ctw = gx > 0 ? ldr(sp.tE[a] + i - 1) : 0.0;
+            cts = gy > 0 ? ldr(sp.tN[a] + i - pitch) : 0.0;
+            po = ldc(sp.pd[a] + i);
+            yo = ldc(sp.z[a] + i);
+          } else {
+            cte = te[j]; ctw = tw[j]; ctn = tn[j]; cts = ts[j]; po = pold[j]; yo = yold[j];
+          }
+          const double* pn = sm.pn + l * PN;
+          const double sn = fma(bt, bS[b], bW[b]);
+          const double rn = pn[c];
+          const double pv = fma(bt, po, bR[b]);
+          const double yv = fma(al, pv, yo);
+          double nb = fma(cte, pn[c + 1], fma(ctw, pn[c - 1], fma(ctn, pn[c + PX], cts * pn[c - PX])));
+          if (C) {
+#pragma unroll
+            for (int bb = 0; bb < L; ++bb) {
+              if (bb == a) continue;
+              nb = fma(ldr(sp.qs[a][bb] + i), sm.pn[bb * PN + c], nb);
+            }
+          }
+          const double wv = rn - nb;
+          (cur ? sp.r[a] : sp.q[a])[i] = rn;
+          sp.P[cur ^ 1][a][i] = sn;
+          sp.w[cur ^ 1][a][i] = wv;
+          sp.pd[a][i] = pv;
+          sp.z[a][i] = yv;
+#pragma unroll
+          for (int kk = 0; kk < L; ++kk)
+            if (kk == a) {
+              dots[kk] = fma(rn, rn, dots[kk]);
+              dots[L + kk] = fma(wv, rn, dots[L + kk]);
+              if (chk) {
+                const double u = ldr(sp.sqd[a] + i) * rn;
+                dots[2 * L + kk] = fma(u, u, dots[2 * L + kk]);
+              }
+            }
+        }
+      }
+      __syncthreads();
+    }
+    if (!tma_ok) {
+      for (int st = 0; st < NST; ++st)
+        if (pend & (1u << st)) mbar_wait(sm.bar + st, (phb >> st) & 1u, 1LL << 24);
+      ok = false;
+      break;
+    }
+    const unsigned qm = chk ? qbits(active, L, 3) : qbits(active, L, 2);
+    block_store<3 * L>(dots, qm, sm.box, sp.partials, slot);
+    if (!grid_sync(sp)) { ok = false; break; }
+    grid_totals<3 * L>(sp.partials, slot, sm.res);
+    slot ^= 1;
+    if (tid == 0) {
+      double sg = 0.0, sd = 0.0, sr = 0.0;
+      for (int a = 0; a < L; ++a) { sg += sm.res[a]; sd += sm.res[L + a]; sr += sm.res[2 * L + a]; }
+      unsigned act = active;
+      int bad = 0;
+      for (int a = 0; a < L; ++a) {
+        const unsigned bit = 1u << a;
+        if (!(active & bit)) continue;
+        const double gam = C ? sg : sm.res[a];
+        const double del = C ? sd : sm.res[L + a];
+        if (!isfinite(gam) || !isfinite(del)) { bad = 1; continue; }
+        if (it >= 0) S.iters[a] = it + 1;
+        if (gam == 0.0) {  // exact solution (tiny grids)
+          S.rr[a] = 0.0;
+          act &= ~bit;
+          continue;
+        }
+        if (chk) {
+          const double rra = C ? sr : sm.res[2 * L + a];
+          S.rr[a] = rra;
+          if (!(rra > rtol2 * S.bb[a])) { act &= ~bit; continue; }
+        }
+        if (it < 0) {
+          if (!(del > 0.0)) { bad = 1; continue; }
+          S.rz[a] = gam;               // gamma of the last pass
+          S.rzl[a] = gam / del;        // alpha of the last pass
+          S.alpha[a] = S.rzl[a];
+          S.beta[a] = 0.0;
+          continue;
+        }
+        const double be = gam / S.rz[a];
+        const double den = del - be * gam / S.rzl[a];
+        if (!(den > 0.0)) { bad = 1; continue; }
+        S.rz[a] = gam;
+        S.rzl[a] = gam / den;
+        S.alpha[a] = S.rzl[a];
+        S.beta[a] = be;
+      }
+      S.active = act;
+      S.flag = bad;
+    }
+    __syncthreads();
+    active = S.active;
+    if (S.flag) {
+      if (blockIdx.x == 0 && tid == 0) atomicCAS(sp.status, 0, (int)MC_E_BREAKDOWN);
+      ok = false;
+      break;
+    }
+    cur ^= 1;
+    ++it;
+  }
+  slot_io = slot;
+  return ok;
+}
+
+template <int L, bool C, bool SP1>
+__device__ bool pcg_solve_scaled(const StepParams& sp, const TmaMaps& maps, unsigned mask, Smem& sm,
+                                 uint32_t& phb) {
+  if (!scaled_init<L, C>(sp, mask, sm, SP1)) return false;
+  int slot = 1;
+  bool ok;
+  if constexpr (SP1) ok = sp1_loop<L, C>(sp, maps, sm, phb, slot);
+  else ok = scaled_loop<L, C>(sp, maps, sm, phb, slot);
+  if (ok) return scaled_finish<L, C>(sp, mask, sm, slot);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // keep the iteration counts of the failed solve
+    const Scal64& S = *sm.sc;
+    for (int a = 0; a < L; ++a) {
+      if (!(mask & (1u << a)) || (C && a != 0)) continue;
+      sp.iters[a] += S.iters[a];
+      if (S.iters[a] > sp.max_iters[a]) sp.max_iters[a] = S.iters[a];
+    }
+  }
+  return false;
+}
+
+// MODE 0: Jacobi PCG, flux-form stencil; 1: two-level preconditioner
+// (decoupled); 2: Jacobi PCG in scaled variables.
+template <int L, bool COUPLED, int MODE>
 __global__ void __launch_bounds__(NT, 1)
     step_kernel(const __grid_constant__ StepParams sp, const __grid_constant__ TmaMaps maps) {
   constexpr int NL = COUPLED ? L : 1;
-  constexpr int NARR = 2 * NL;
-  constexpr int NST = nstage(L, COUPLED);
+  constexpr int NARR = (MODE == 3 ? 3 : 2) * NL;
+  constexpr int NST = MODE == 3 ? nstage1(L, COUPLED) : nstage(L, COUPLED);
+  constexpr int NPN = (MODE == 2 && !COUPLED) ? 2 : 1;  // P_new areas (scaled_loop)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // TMA destinations need 128-B aligned slots: align the dynamic base.
   unsigned char* smem_base = reinterpret_cast<unsigned char*>(
@@ -825,7 +1665,7 @@ __global__ void __launch_bounds__(NT, 1)
   sm.cn = s_cn;
   sm.box = reinterpret_cast<double*>(smem_base);
   sm.pn = sm.box + NST * NARR * ABOX;
-  sm.red = sm.pn + NL * PN;
+  sm.red = sm.pn + NPN * NL * PN;
   sm.res = sm.red + (NT / 32) * KMAX;
   sm.bar = reinterpret_cast<uint64_t*>(sm.res + KMAX);
   if (threadIdx.x == 0) {
@@ -845,13 +1685,16 @@ __global__ void __launch_bounds__(NT, 1)
     for (int a = 0; a < L; ++a)
       for (long long i = gtid; i < Np; i += gstride) sp.pprev[a][i] = ldc(sp.p[a] + i);
     if (COUPLED) {
-      ok = pcg_solve<L, true, false>(sp, maps, (1u << L) - 1u, sm, phb);
+      if (MODE >= 2) ok = pcg_solve_scaled<L, true, MODE == 3>(sp, maps, (1u << L) - 1u, sm, phb);
+      else ok = pcg_solve<L, true, false>(sp, maps, (1u << L) - 1u, sm, phb);
     } else if (sp.scheme == MC_SCHEME_D) {
-      ok = pcg_solve<L, false, TLV>(sp, maps, (1u << L) - 1u, sm, phb);
+      if (MODE >= 2) ok = pcg_solve_scaled<L, false, MODE == 3>(sp, maps, (1u << L) - 1u, sm, phb);
+      else ok = pcg_solve<L, false, MODE == 1>(sp, maps, (1u << L) - 1u, sm, phb);
     } else {
       for (int k = 0; k < L && ok; ++k) {
         const int a = sp.scheme == MC_SCHEME_U ? L - 1 - k : k;
-        ok = pcg_solve<L, false, TLV>(sp, maps, 1u << a, sm, phb);
+        if (MODE >= 2) ok = pcg_solve_scaled<L, false, MODE == 3>(sp, maps, 1u << a, sm, phb);
+        else ok = pcg_solve<L, false, MODE == 1>(sp, maps, 1u << a, sm, phb);
       }
     }
     if (ok) ++done;
@@ -898,11 +1741,13 @@ __global__ void __launch_bounds__(NT, 1)
   }
 }
 
-template <int L, bool C>
+template <int L, bool C, int M>
 constexpr size_t smem_bytes() {
   constexpr int NL = C ? L : 1;
-  constexpr int NST = nstage(L, C);
-  return (size_t)(NST * 2 * NL * ABOX + NL * PN + (NT / 32) * KMAX + KMAX) * sizeof(double) +
+  constexpr int NST = M == 3 ? nstage1(L, C) : nstage(L, C);
+  constexpr int NB = M == 3 ? 3 : 2;
+  constexpr int NPN = (M == 2 && !C) ? 2 : 1;
+  return (size_t)(NST * NB * NL * ABOX + NPN * NL * PN + (NT / 32) * KMAX + KMAX) * sizeof(double) +
          NST * sizeof(uint64_t) + 128;
 }
 
@@ -911,19 +1756,32 @@ struct KInfo {
   size_t smem;
 };
 
-// The two-level variant is a separate instantiation, so that the Jacobi
-// kernel carries none of its code.
-template <int L, bool C, bool T>
+// Each variant (flux-form Jacobi, two-level, scaled Jacobi, coupled) is a
+// separate instantiation, so that no kernel carries another's code.
+template <int L, bool C, int M>
 KInfo info() {
-  return KInfo{(void*)step_kernel<L, C, T>, smem_bytes<L, C>()};
+  return KInfo{(void*)step_kernel<L, C, M>, smem_bytes<L, C, M>()};
 }
 
-KInfo pick(int L, bool coupled, bool two_level = false) {
+template <int L>
+KInfo pick_l(bool coupled, int mode) {
+  if (coupled) return mode == 3 ? info<L, true, 3>() : (mode == 2 ? info<L, true, 2>() : info<L, true, 0>());
+  switch (mode) {
+    case 1: return info<L, false, 1>();
+    case 2: return info<L, false, 2>();
+    case 3: return info<L, false, 3>();
+    default: return info<L, false, 0>();
+  }
+}
+
+// mode: 0 flux-form Jacobi, 1 two-level (decoupled only), 2 scaled Jacobi
+// (two phases, two reductions per iteration), 3 scaled Jacobi single-pass
+KInfo pick(int L, bool coupled, int mode = 0) {
   switch (L) {
-    case 1: return coupled ? info<1, true, false>() : (two_level ? info<1, false, true>() : info<1, false, false>());
-    case 2: return coupled ? info<2, true, false>() : (two_level ? info<2, false, true>() : info<2, false, false>());
-    case 3: return coupled ? info<3, true, false>() : (two_level ? info<3, false, true>() : info<3, false, false>());
-    default: return coupled ? info<4, true, false>() : (two_level ? info<4, false, true>() : info<4, false, false>());
+    case 1: return pick_l<1>(coupled, mode);
+    case 2: return pick_l<2>(coupled, mode);
+    case 3: return pick_l<3>(coupled, mode);
+    default: return pick_l<4>(coupled, mode);
   }
 }
 
@@ -987,11 +1845,16 @@ cudaError_t mc_launch_coarse_assemble(const mc_ctx* ctx, int a, double* Ac) {
 }
 
 int mc_step_max_blocks(int L, int threads, int num_sms) {
-  const int a0 = max_blocks_for(pick(L, false), threads, num_sms);
-  const int a1 = max_blocks_for(pick(L, false, true), threads, num_sms);
-  const int a = a0 < a1 ? a0 : a1;
-  const int b = max_blocks_for(pick(L, true), threads, num_sms);
-  return a < b ? a : b;
+  int m = max_blocks_for(pick(L, true), threads, num_sms);
+  for (int mode = 2; mode < 4; ++mode) {
+    const int c = max_blocks_for(pick(L, true, mode), threads, num_sms);
+    if (c < m) m = c;
+  }
+  for (int mode = 0; mode < 4; ++mode) {
+    const int a = max_blocks_for(pick(L, false, mode), threads, num_sms);
+    if (a < m) m = a;
+  }
+  return m;
 }
 
 int mc_step_box_x() { return BX; }
@@ -1003,7 +1866,8 @@ cudaError_t mc_launch_steps_raw(const StepParams& sp_in, const TmaMaps& maps_in,
   TmaMaps maps = maps_in;
   sp.tiles_x = (sp.nx + TX - 1) / TX;
   sp.tiles_y = (sp.ny + TY - 1) / TY;
-  KInfo k = pick(sp.L, sp.scheme == MC_SCHEME_COUPLED, sp.two_level != 0);
+  const int mode = sp.two_level ? 1 : (sp.sqd[0] == nullptr ? 0 : (sp.single_pass ? 3 : 2));
+  KInfo k = pick(sp.L, sp.scheme == MC_SCHEME_COUPLED, mode);
   cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
   if (e != cudaSuccess) return e;
   void* args[] = {&sp, &maps};

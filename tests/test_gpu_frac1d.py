@@ -1,0 +1,137 @@
+"""GPU parity of the lower-dimensional fracture continuum (Section 2, Eqs.
+mm-md / mm-tc; Section 3.1, Eqs. app-md / app-tc) against the oracle.
+
+The mesh the library builds must match the oracle's piece by piece (count,
+host cells exactly; lengths and midpoints to roundoff). The D-, L-, U- and
+coupled steps must match the oracle's exact solves at the FP64 bar: relative
+L2 over all matrix cells and pieces jointly, and the elementwise error
+max|p - p_ref| / max|p_ref|, both <= 1e-10 at rtol 1e-12.
+"""
+
+import numpy as np
+import pytest
+
+import mc_inputs as mi
+from oracle.fracture1d import FractureMesh, from_workload as oracle_frac
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def mc():
+    import paper_2209_01158_gb300 as m
+    m._lib()
+    return m
+
+
+def _errs(ref, got):
+    r = np.concatenate([np.ravel(x) for x in ref])
+    g = np.concatenate([np.ravel(x) for x in got])
+    return (float(np.linalg.norm(r - g) / np.linalg.norm(r)),
+            float(np.max(np.abs(r - g)) / np.max(np.abs(r))))
+
+
+def _pair(mc, w, rtol=1e-12):
+    o = mc.mc_default_opts()
+    o.rtol = rtol
+    ctx = mc.Context.from_workload(w, opts=o)
+    f = mc.Fracture.from_workload(ctx, w)
+    return ctx, f
+
+
+MESH_CASES = [("paper2c_200", lambda: mi.fracture1d(1, n=200)),
+              ("src_L1_128", lambda: mi.fracture1d_sources(1, n=128)),
+              ("src_L2_96", lambda: mi.fracture1d_sources(2, n=96))]
+
+
+@pytest.mark.parametrize("name,make", MESH_CASES)
+def test_mesh_matches_oracle(mc, name, make):
+    w = make()
+    ctx, f = _pair(mc, w)
+    ln, mid, host = f.pieces()
+    m = FractureMesh(w.frac.segments, w.nx, w.ny)
+    assert f.P == m.P
+    np.testing.assert_array_equal(host, m.host)
+    np.testing.assert_allclose(ln, m.length, rtol=1e-13)
+    np.testing.assert_allclose(mid, m.mid, rtol=0, atol=1e-15)
+    info = f.info()
+    assert info["junctions"] == len(m.junctions)
+    f.close()
+    ctx.close()
+
+
+STEP_CASES = [
+    ("paper2c_60", lambda: mi.fracture1d(1, n=60), 4),
+    ("paper3c_60", lambda: mi.fracture1d(2, n=60), 4),
+    ("src_L1_72", lambda: mi.fracture1d_sources(1, n=72, nsteps=4), 4),
+    ("src_L2_66", lambda: mi.fracture1d_sources(2, n=66, nsteps=4), 4),
+]
+
+
+@pytest.mark.parametrize("scheme", ["D", "L", "U"])
+@pytest.mark.parametrize("name,make,nsteps", STEP_CASES)
+def test_decoupled_schemes_match_oracle(mc, name, make, nsteps, scheme):
+    w = make()
+    o, p0 = oracle_frac(w)
+    ref = o.run(p0, w.F, nsteps, scheme)
+    ctx, f = _pair(mc, w)
+    st = f.step(scheme, nsteps)
+    pm, pf = f.get_state()
+    f.close()
+    ctx.close()
+    e2, emax = _errs(ref, pm + [pf])
+    assert e2 <= TOL and emax <= TOL, (e2, emax, st)
+    assert st["steps_done"] == nsteps and st["iters"][w.L] > 0
+
+
+@pytest.mark.parametrize("name,make,nsteps", STEP_CASES[:3])
+def test_coupled_scheme_matches_oracle(mc, name, make, nsteps):
+    w = make()
+    o, p0 = oracle_frac(w)
+    ref = o.run(p0, w.F, nsteps, "coupled")
+    ctx, f = _pair(mc, w)
+    st = f.step("coupled", nsteps)
+    pm, pf = f.get_state()
+    f.close()
+    ctx.close()
+    e2, emax = _errs(ref, pm + [pf])
+    assert e2 <= TOL and emax <= TOL, (e2, emax, st)
+
+
+def test_full_size_d_scheme(mc):
+    """The point-source workload at 1024^2 (the benchmark's fracture line),
+    two D-scheme steps against the oracle. The second matrix solve is driven
+    only by the exchange with the fracture (a right-hand side on the hosting
+    cells, a small mass term elsewhere): at rtol 1e-12 its forward error is
+    5e-10 (CPU emulation of the same Jacobi PCG: 5.1e-10 in 1518 iterations),
+    so the FP64 bar needs rtol 1e-13 here (3.1e-11 in the emulation)."""
+    w = mi.fracture1d_sources(1, n=1024, nsteps=2)
+    o, p0 = oracle_frac(w)
+    ref = o.run(p0, w.F, 2, "D")
+    ctx, f = _pair(mc, w, rtol=1e-13)
+    st = f.step("D", 2)
+    pm, pf = f.get_state()
+    f.close()
+    ctx.close()
+    e2, emax = _errs(ref, pm + [pf])
+    assert e2 <= TOL and emax <= TOL, (e2, emax, st)
+
+
+def test_failure_keeps_start_of_step(mc):
+    """max_iter = 1: the first solve fails (MC_E_NOCONV) and both the matrix
+    and the fracture state stay at the start of the step."""
+    w = mi.fracture1d(1, n=40)
+    o = mc.mc_default_opts()
+    o.max_iter = 1
+    ctx = mc.Context.from_workload(w, opts=o)
+    f = mc.Fracture.from_workload(ctx, w)
+    pm0, pf0 = f.get_state()
+    st = f.step("D", 2, check=False)
+    assert st["return"] == mc.N.MC_E_NOCONV and st["steps_done"] == 0
+    pm, pf = f.get_state()
+    np.testing.assert_array_equal(pm[0], pm0[0])
+    np.testing.assert_array_equal(pf, pf0)
+    f.close()
+    ctx.close()

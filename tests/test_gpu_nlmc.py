@@ -91,12 +91,7 @@ def test_basis_operator_and_runs(mc, name, make, ncx, layers):
             ref = R[beta * Nc + i]
             got = nl.basis(i, beta)
             worst = max(worst, np.linalg.norm(got - ref) / np.linalg.norm(ref))
-    # With a support mask the fracture continuum's cells outside Omega_f
-    # (k = 1e-2, no exchange) are unconstrained: the local problems are about
-    # 1e6 times stiffer than with whole-block constraints, and the same
-    # 1e-12 basis tolerance leaves basis errors of a few 1e-9 (measured
-    # 1.1e-9 .. 5.5e-9); A_bar and the coarse runs keep their bars.
-    assert worst < (1e-8 if support else 1e-9), worst
+    assert worst < 1e-9, worst
     A, m, f = nl.operator()
     np.testing.assert_allclose(A, onl.Abar, rtol=0, atol=1e-9 * np.abs(onl.Abar).max())
     np.testing.assert_allclose(m, onl.mbar, rtol=1e-14)
