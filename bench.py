@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-extras", action="store_true", help="only the headline D-scheme line")
+    ap.add_argument("--only", default=None, metavar="LIST",
+                    help="comma-separated extra lines to run (coupled, single_pass, two_level, ir, "
+                         "nlmc, frac1d, precision, paper, batched); default all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--crop", type=int, default=384, help="oracle sample size (cells per side)")
     ap.add_argument("--batch", type=int, default=64,
@@ -389,6 +392,28 @@ def batched_extra(args, mc, mi, torch, stream, ws, precond=0):
     for x in wb:
         sizes["%dx%d_L%d" % (x.nx, x.ny, x.L)] = sizes.get("%dx%d_L%d" % (x.nx, x.ny, x.L), 0) + 1
     bt.close()
+    # the coupled FP64 solve (PCG with the same preconditioner as the FP64
+    # path, rtol 1e-12: at least the batch's accuracy) on the same instances,
+    # one step each from their current state, CUDA events around every call,
+    # summed
+    o64 = mc.mc_default_opts()
+    o64.rtol = RTOL_BATCH
+    o64.precond = precond
+    ctxs[0].set_opts(o64)
+    ctxs[0].step("coupled", 1)
+    ct, its = 0.0, 0
+    for c in ctxs:
+        c.set_opts(o64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s = c.step("coupled", 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ct += e0.elapsed_time(e1) * 1e-3
+        its += s["iters"][0]
+    coupled = {"s_per_step": ct, "pcg_iterations_per_step": its,
+               "batched_speedup_vs_coupled": ct / (dt / args.batch_steps)}
     for c in ctxs:
         c.close()
     return {"workload": "batched fracture instances, seeds 4000..%d (sizes %s), D-scheme, FP32 "
@@ -403,7 +428,8 @@ def batched_extra(args, mc, mi, torch, stream, ws, precond=0):
             "fp64_instances": info["fp64_instances"],
             "inner_iterations_per_step": float(sum(st["iters"])) / args.batch_steps,
             "ir_sweeps_per_step": st["ir_sweeps"] / args.batch_steps,
-            "max_final_rel_residual": relres}
+            "max_final_rel_residual": relres,
+            "coupled_fp64_same_instances": coupled}
 
 
 def support_means(fields, sup, nc):
@@ -566,6 +592,7 @@ def summary_of(value, roof, e2e, extras):
         "fp64_single_pass_value": g("fp64_single_pass", "value"),
         "two_level_value": g("fp64_two_level", "value"),
         "two_level_speedup_vs_coupled": g("fp64_two_level", "speedup_vs_coupled"),
+        "two_level_speedup_vs_coupled_two_level": g("fp64_two_level", "speedup_vs_coupled_two_level"),
         "fp32_ir_value": g("fp32_ir", "value"), "fp32_ir_hbm_frac": g("fp32_ir", "roofline_inner", "frac"),
         "bf16t_ir_value": g("bf16t_ir", "value"),
         "p4096_fp32_hbm_frac": g("precision_4096", "fp32", "roofline_inner", "frac"),
@@ -579,6 +606,9 @@ def summary_of(value, roof, e2e, extras):
         "frac1d_2c_e_h_pct_D": g("frac1d", "paper_2c", "D", "e_h_percent"),
         "frac1d_1024_D_speedup_vs_coupled": g("frac1d", "points_1024", "decoupled_D_speedup"),
         "batched_value": g("batched", "value"), "batched_fp64_instances": g("batched", "fp64_instances"),
+        "batched_two_level_value": g("batched_two_level_fp64", "value"),
+        "batched_speedup_vs_coupled": g("batched", "coupled_fp64_same_instances",
+                                        "batched_speedup_vs_coupled"),
     })
     return s
 
@@ -676,13 +706,20 @@ def main():
                          "unit": "GB/s", "peak_kind": pk["hbm_kind"],
                          "frac": BYTES_PER_CELL_IT * cell_its / dev_time / 1e9 / hbm}}
 
+    only = None if args.only is None else set(args.only.split(","))
+
+    def want(name):
+        return not args.no_extras and (only is None or name in only)
+
     extras = {}
-    if not args.no_extras:
+    cdev = None
+    if want("coupled") or want("two_level"):
         cdev, cits, _ = timed_run("coupled", opts_for(RTOL_COUPLED))
         extras["coupled"] = {"value": ws * cells_steps / cdev, "unit": "continuum-cell updates/s",
                              "ms_per_step": 1e3 * cdev / args.steps, "rtol": RTOL_COUPLED,
                              "pcg_iterations_per_step": float(np.mean(cits)),
                              "decoupled_speedup": cdev / dev_time}
+    if want("single_pass"):
         # the same scaled Jacobi PCG with the single-pass (one reduction) iteration
         rdev, rits, _ = timed_run("D", opts_for(RTOL_D, fp64_form=1))
         extras["fp64_single_pass"] = {
@@ -690,6 +727,7 @@ def main():
             "ms_per_step": 1e3 * rdev / args.steps, "rtol": RTOL_D,
             "pcg_iterations_per_step": float(np.mean(rits)),
             "speedup_vs_two_pass": dev_time / rdev}
+    if want("two_level"):
         try:
             tdev, tits, _ = timed_run("D", opts_for(RTOL_D, precond=1))
             tci = float(sum(tits)) * Ncell
@@ -701,8 +739,16 @@ def main():
                 "pcg_iterations_per_step": float(np.mean(tits)),
                 "speedup_vs_jacobi": dev_time / tdev,
                 "speedup_vs_coupled": cdev / tdev}
+            # the coupled scheme with the same coarse spaces (block-diagonal)
+            udev, uits, _ = timed_run("coupled", opts_for(RTOL_COUPLED, precond=1))
+            extras["fp64_two_level"]["coupled"] = {
+                "value": ws * cells_steps / udev, "unit": "continuum-cell updates/s",
+                "ms_per_step": 1e3 * udev / args.steps, "rtol": RTOL_COUPLED,
+                "pcg_iterations_per_step": float(np.mean(uits))}
+            extras["fp64_two_level"]["speedup_vs_coupled_two_level"] = udev / tdev
         except Exception as e:  # report, do not abort the benchmark
             extras["fp64_two_level"] = {"error": str(e)}
+    if want("ir"):
         for name, prec, form in (("fp32_ir", 1, 0), ("bf16t_ir", 2, 0),
                                  ("fp32_ir_two_reductions", 1, 1)):
             pdev, pits, psw = timed_run("D", opts_for(RTOL_D, prec, form))
@@ -740,18 +786,19 @@ def main():
     e2e = {"value": ws * cells_steps / et, "unit": "continuum-cell updates/s",
            "h2d_bytes_per_step": 8 * L * Ncell, "d2h_bytes_per_step": 8 * L * Ncell}
 
-    if not args.no_extras:
+    if want("nlmc"):
         extras["nlmc"] = nlmc_extra(args, mc, mi, torch, stream, opts_for)
         extras["nlmc_paper_2c"] = nlmc_paper_extra(mc, mi, opts_for)
-
-    if not args.no_extras:
+    if want("frac1d"):
         try:
             extras["frac1d"] = frac1d_extra(args, mc, mi, torch, stream, opts_for)
         except Exception as e:  # report, do not abort the benchmark
             extras["frac1d"] = {"error": str(e)}
+    if want("precision"):
         extras["precision_4096"] = precision_extra(args, mc, mi, torch, stream, ws, hbm)
+    if want("paper"):
         extras["paper_wells"] = paper_extra(args, mc, mi, np)
-    if not args.no_extras and args.batch > 0:
+    if want("batched") and args.batch > 0:
         extras["batched"] = batched_extra(args, mc, mi, torch, stream, ws)
         try:
             extras["batched_two_level_fp64"] = batched_extra(args, mc, mi, torch, stream, ws, precond=1)

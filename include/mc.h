@@ -66,14 +66,19 @@ typedef struct {
 } mc_grid;
 
 enum { MC_PREC_FP64 = 0, MC_PREC_FP32_IR = 1, MC_PREC_BF16T_IR = 2 };
-/* Preconditioners of the FP64 PCG. MC_PRECOND_TWO_LEVEL (decoupled FP64
-   schemes only) adds to Jacobi a Galerkin coarse correction on the 64 x 16
-   stencil tiles, M^-1 = D^-1 + P (P^T A P)^-1 P^T with P the tile
-   indicators; its dense inverse is formed on the device at the first step
-   (at most MC_TWO_LEVEL_MAX_TILES tiles per continuum, else MC_E_ARG). It
-   changes only the Krylov iteration, not the system solved. */
+/* Preconditioners of the FP64 PCG. MC_PRECOND_TWO_LEVEL (FP64 schemes
+   only) adds to Jacobi a Galerkin coarse correction on the 64 x 16 stencil
+   tiles, M^-1 = D^-1 + P (P^T A P)^-1 P^T with P the tile indicators; its
+   dense inverse is formed on the device at the first step (at most
+   MC_TWO_LEVEL_MAX_TILES tiles per continuum, else MC_E_ARG). The coupled
+   scheme takes the coarse space P = blockdiag(P_a) with the Galerkin operator
+   of the coupled matrix, exchange blocks included: M^-1 = D^-1 +
+   P (P^T A P)^-1 P^T, an (L nc)^2 dense inverse (L nc at most
+   MC_TWO_LEVEL_MAX_COUPLED, else MC_E_ARG). It changes only the Krylov
+   iteration, not the system solved. */
 enum { MC_PRECOND_JACOBI = 0, MC_PRECOND_TWO_LEVEL = 1 };
 #define MC_TWO_LEVEL_MAX_TILES 2048
+#define MC_TWO_LEVEL_MAX_COUPLED 4096
 /* Inner FP32 PCG of the IR forms: single-reduction (Chronopoulos-Gear)
    recurrences, one grid-wide reduction per iteration, or the textbook
    (Hestenes-Stiefel) recurrences with two. Both are the Jacobi PCG of

@@ -15,6 +15,7 @@ MC_OK, MC_E_ARG, MC_E_ALLOC, MC_E_CUDA, MC_E_NOCONV, MC_E_TIMEOUT, MC_E_STATE, M
 MC_PREC_FP64, MC_PREC_FP32_IR, MC_PREC_BF16T_IR = 0, 1, 2
 MC_PRECOND_JACOBI, MC_PRECOND_TWO_LEVEL = 0, 1
 MC_TWO_LEVEL_MAX_TILES = 2048
+MC_TWO_LEVEL_MAX_COUPLED = 4096
 MC_INNER_SINGLE_REDUCTION, MC_INNER_TWO_REDUCTIONS = 0, 1
 MC_NLMC_CONSERVATIVE = 1
 MC_FP64_TWO_PASS, MC_FP64_SINGLE_PASS = 0, 1

@@ -441,6 +441,7 @@ mc_status mc_set_well(mc_ctx* ctx, int32_t alpha, const double* W, const double*
   CK(mc_launch_pairs(ctx));
   ctx->lo_kind = 0;  // FP32 / BF16 copies of diag and invd are stale
   ctx->tl_ready = 0;  // so is the two-level coarse operator
+  ctx->tl_full_ready = 0;
   CK(cudaStreamSynchronize(ctx->stream));
   return MC_OK;
 }
@@ -475,12 +476,17 @@ mc_status mc_state_device(mc_ctx* ctx, int32_t alpha, double** dev) {
 
 // Two-level preconditioner set-up: the coarse operator of every continuum on
 // the stencil tiles and its dense inverse (Gauss-Jordan on the device), once
-// per context and again after the diagonal changes (mc_set_well).
-static mc_status tl_prepare(mc_ctx* ctx) {
-  if (ctx->tl_ready) return MC_OK;
+// per context and again after the diagonal changes (mc_set_well); for the
+// coupled scheme the Galerkin operator over all continua instead.
+static mc_status tl_prepare_coupled(mc_ctx* ctx);
+
+static mc_status tl_prepare(mc_ctx* ctx, bool coupled) {
   const int nc = mc_step_tiles(ctx->nx, ctx->ny);
   if (nc > MC_TWO_LEVEL_MAX_TILES)
     return set_err(ctx, MC_E_ARG, "two-level preconditioner: more than MC_TWO_LEVEL_MAX_TILES tiles");
+  if (coupled && (long long)ctx->L * nc > MC_TWO_LEVEL_MAX_COUPLED)
+    return set_err(ctx, MC_E_ARG, "two-level preconditioner: L x tiles above MC_TWO_LEVEL_MAX_COUPLED");
+  if (ctx->tl_ready) return coupled ? tl_prepare_coupled(ctx) : MC_OK;
   if (!ctx->tl_work) {
     CK(mc_alloc(ctx, (void**)&ctx->tl_work, 2 * (size_t)nc * sizeof(double)));
     CK(mc_alloc(ctx, (void**)&ctx->tl_bar, 96 * sizeof(unsigned)));
@@ -502,6 +508,25 @@ static mc_status tl_prepare(mc_ctx* ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   if (st != MC_OK) return set_err(ctx, (mc_status)st, "two-level preconditioner set-up");
   ctx->tl_ready = 1;
+  return coupled ? tl_prepare_coupled(ctx) : MC_OK;
+}
+
+static mc_status tl_prepare_coupled(mc_ctx* ctx) {
+  if (ctx->tl_full_ready) return MC_OK;
+  const long long n = (long long)ctx->L * ctx->tl_nc;
+  if (!ctx->tl_Afull) {
+    CK(mc_alloc(ctx, (void**)&ctx->tl_Afull, (size_t)(n * n) * sizeof(double)));
+    CK(mc_alloc(ctx, (void**)&ctx->tl_work_full, 2 * (size_t)n * sizeof(double)));
+  }
+  CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), ctx->stream));
+  CK(mc_launch_coarse_assemble_coupled(ctx, ctx->tl_Afull));
+  CK(mc_gj_invert(ctx->tl_Afull, (int)n, ctx->tl_work_full, ctx->tl_bar, ctx->dstatus, ctx->opts.spin_limit,
+                  ctx->num_sms, ctx->stream));
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st != MC_OK) return set_err(ctx, (mc_status)st, "two-level preconditioner set-up (coupled)");
+  ctx->tl_full_ready = 1;
   return MC_OK;
 }
 
@@ -512,12 +537,12 @@ static mc_status run_steps(mc_ctx* ctx, int scheme, int nsteps, mc_stats* stats)
   if (ir && scheme == MC_SCHEME_COUPLED)
     return set_err(ctx, MC_E_ARG, "the precision form applies to the decoupled schemes");
   const bool tl = ctx->opts.precond == MC_PRECOND_TWO_LEVEL;
-  if (tl && (ir || scheme == MC_SCHEME_COUPLED))
-    return set_err(ctx, MC_E_ARG, "the two-level preconditioner applies to the FP64 decoupled schemes");
+  if (tl && ir)
+    return set_err(ctx, MC_E_ARG, "the two-level preconditioner applies to the FP64 schemes");
   if (nsteps == 0) return MC_OK;
   CK(cudaSetDevice(ctx->device));
   if (tl) {
-    const mc_status ps = tl_prepare(ctx);
+    const mc_status ps = tl_prepare(ctx, scheme == MC_SCHEME_COUPLED);
     if (ps != MC_OK) return ps;
   }
   StepParams sp;
@@ -529,6 +554,10 @@ static mc_status run_steps(mc_ctx* ctx, int scheme, int nsteps, mc_stats* stats)
       sp.Ainv[a] = ctx->tl_Ainv[a];
       sp.gsum[a] = ctx->tl_g[a];
       sp.ccor[a] = ctx->tl_c[a];
+    }
+    if (scheme == MC_SCHEME_COUPLED) {
+      sp.tl_full = 1;
+      sp.Ainv[0] = ctx->tl_Afull;
     }
   }
   CK(cudaMemsetAsync(ctx->bar, 0, 96 * sizeof(unsigned), ctx->stream));

@@ -95,8 +95,12 @@ struct mc_frac {
   double* cpart = nullptr;   // coupled kernel partial sums
   unsigned* cbar = nullptr;  // coupled kernel barrier words
   int* hidx = nullptr;       // per pitched matrix cell: hosting-cell list index or -1
-  double* Pf2 = nullptr;     // second search-direction buffer of the coupled kernel
+  double* Pf2 = nullptr;     // second search-direction buffer (coupled and grid fracture kernels)
   int cblocks = 0;
+  double* gpart = nullptr;   // grid fracture solve: partial sums
+  unsigned* gbar = nullptr;  // grid fracture solve: barrier words
+  int gblocks = 0;           // grid fracture solve: CTAs of the launch
+  int gcap = 0;              // grid fracture solve: co-resident CTAs
   std::vector<void*> allocs;
   int64_t bytes = 0;
 };
@@ -350,19 +354,73 @@ __global__ void frac_line_factor_kernel(int NS, const int* segptr, const int* ro
   }
 }
 
-// z = M^-1 r on the pieces l0..l1-1 of one segment (forward and back
-// substitution with the stored factors).
-__device__ __forceinline__ void line_apply(int l0, int l1, const double* lo, const double* cp,
-                                           const double* dinv, const double* r, double* z) {
-  double y = 0.0;
-  for (int l = l0; l < l1; ++l) {
-    y = (r[l] - lo[l] * y) * dinv[l];
+// z = M^-1 r on the pieces l0..l1-1 of one segment, by one warp (all 32 lanes
+// call it). Forward substitution y_l = (r_l - lo_l y_{l-1}) dinv_l and back
+// substitution z_l = y_l - cp_l z_{l+1} are affine recurrences x_l = a_l +
+// b_l x_prev. Lane k owns the contiguous run [k m, (k+1) m) of the segment,
+// m = ceil(n / 32): it composes the maps of its run (compose (a2, b2) after
+// (a1, b1): (a2 + b2 a1, b2 b1)), an inclusive warp scan of the 32 run maps
+// (5 shuffle steps) gives every run its incoming value, and a second walk over
+// the run writes the results. Each lane's walk is one dependent FMA chain over
+// independent loads, so a long segment costs about 4 m FMA latencies rather
+// than a load round trip per 32 pieces. |b_l| < 1 (diagonal dominance), so
+// the products only shrink.
+__device__ __forceinline__ void line_apply_warp(int l0, int l1, const double* lo, const double* cp,
+                                                const double* dinv, const double* r, double* z) {
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  const int n = l1 - l0;
+  const int m = (n + 31) >> 5;
+  const int s0 = l0 + min(n, lane * m), s1 = l0 + min(n, (lane + 1) * m);
+  // forward: y_l = A_l + B_l y_{l-1}, A_l = r_l dinv_l, B_l = -lo_l dinv_l
+  double a = 0.0, b = 1.0;
+#pragma unroll 4
+  for (int l = s0; l < s1; ++l) {
+    const double di = __ldg(dinv + l);
+    a = fma(-__ldg(lo + l) * di, a, __ldcg(r + l) * di);
+    b *= -__ldg(lo + l) * di;
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double ap = __shfl_up_sync(full, a, o), bp = __shfl_up_sync(full, b, o);
+    if (lane >= o) {
+      a = fma(b, ap, a);
+      b *= bp;
+    }
+  }
+  double y = __shfl_up_sync(full, a, 1);  // y before the run (0 before the segment)
+  if (lane == 0) y = 0.0;
+#pragma unroll 4
+  for (int l = s0; l < s1; ++l) {
+    const double di = __ldg(dinv + l);
+    y = fma(-__ldg(lo + l) * di, y, __ldcg(r + l) * di);
     z[l] = y;
   }
-  for (int l = l1 - 2; l >= l0; --l) {
-    y = z[l] - cp[l] * y;
-    z[l] = y;
+  // backward: z_l = y_l + B'_l z_{l+1}, B'_l = -cp_l, walked from the run's end
+  a = 0.0;
+  b = 1.0;
+#pragma unroll 4
+  for (int l = s1 - 1; l >= s0; --l) {
+    const double bl = -__ldg(cp + l);
+    a = fma(bl, a, z[l]);
+    b *= bl;
   }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double ad = __shfl_down_sync(full, a, o), bd = __shfl_down_sync(full, b, o);
+    if (lane + o < 32) {
+      a = fma(b, ad, a);
+      b *= bd;
+    }
+  }
+  double x = __shfl_down_sync(full, a, 1);  // z after the run (0 after the segment)
+  if (lane == 31) x = 0.0;
+#pragma unroll 4
+  for (int l = s1 - 1; l >= s0; --l) {
+    x = fma(-__ldg(cp + l), x, z[l]);
+    z[l] = x;
+  }
+  __syncwarp();
 }
 
 struct HostArgs {
@@ -449,8 +507,8 @@ __global__ void __launch_bounds__(FT, 1) frac_solve_kernel(const FracSolve A) {
   }
   __syncthreads();
   // z = M^-1 r (line blocks), p = z, (r, z)
-  for (int s = threadIdx.x; s < A.NS; s += FT)
-    line_apply(A.segptr[s], A.segptr[s + 1], A.llo, A.lcp, A.ldinv, A.r, A.z);
+  for (int s = threadIdx.x >> 5; s < A.NS; s += FT / 32)
+    line_apply_warp(A.segptr[s], A.segptr[s + 1], A.llo, A.lcp, A.ldinv, A.r, A.z);
   __syncthreads();
   for (int l = threadIdx.x; l < P; l += FT) {
     A.p[l] = A.z[l];
@@ -484,8 +542,8 @@ __global__ void __launch_bounds__(FT, 1) frac_solve_kernel(const FracSolve A) {
       d2[0] += rv * rv;
     }
     __syncthreads();
-    for (int s = threadIdx.x; s < A.NS; s += FT)
-      line_apply(A.segptr[s], A.segptr[s + 1], A.llo, A.lcp, A.ldinv, A.r, A.z);
+    for (int s = threadIdx.x >> 5; s < A.NS; s += FT / 32)
+      line_apply_warp(A.segptr[s], A.segptr[s + 1], A.llo, A.lcp, A.ldinv, A.r, A.z);
     __syncthreads();
     for (int l = threadIdx.x; l < P; l += FT) d2[1] += A.r[l] * A.z[l];
     cta_sum<2>(d2, s_red, s_res);
@@ -609,6 +667,13 @@ mc_status matrix_step(mc_frac* f, int scheme, mc_stats* st) {
   return MC_OK;
 }
 
+// Networks of at least this many pieces take the fracture solve over a
+// cooperative grid (frac_solve_grid_kernel); smaller ones the one-CTA kernel,
+// whose CTA barriers are cheaper than grid barriers.
+constexpr int FRAC_GRID_MIN_PIECES = 8192;
+
+mc_status frac_solve_grid(mc_frac* f, const FracSolve& A);
+
 mc_status frac_solve(mc_frac* f, double* const* pm, mc_stats* st) {
   mc_ctx* ctx = f->ctx;
   cudaStream_t s = ctx->stream;
@@ -646,8 +711,13 @@ mc_status frac_solve(mc_frac* f, double* const* pm, mc_stats* st) {
   A.stat = f->dstat;
   A.relres = f->drel;
   if (cudaMemsetAsync(f->dstat, 0, 2 * sizeof(int), s) != cudaSuccess) return ferr(f, MC_E_CUDA, "memset");
-  frac_solve_kernel<<<1, FT, 0, s>>>(A);
-  if (cudaGetLastError() != cudaSuccess) return ferr(f, MC_E_CUDA, "fracture solve launch");
+  if (f->P >= FRAC_GRID_MIN_PIECES) {
+    const mc_status gs = frac_solve_grid(f, A);
+    if (gs != MC_OK) return gs;
+  } else {
+    frac_solve_kernel<<<1, FT, 0, s>>>(A);
+    if (cudaGetLastError() != cudaSuccess) return ferr(f, MC_E_CUDA, "fracture solve launch");
+  }
   int ss[2] = {0, 0};
   double rel = 0.0;
   if (cudaMemcpyAsync(ss, f->dstat, sizeof(ss), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1181,10 +1251,12 @@ __global__ void __launch_bounds__(CT) frac_coupled_kernel(const __grid_constant_
       acc[1] += rv * rv;
       acc[2] += rv * zv;
     }
-  // fracture rows by segment (one thread each): residual, then the line block
-  for (long long s = gt; s < A.NS; s += gs) {
+  // fracture rows by segment (one warp each): residual, then the line block
+  const int lane = threadIdx.x & 31;
+  const long long gwarp = gt >> 5, nwarp = gs >> 5;
+  for (long long s = gwarp; s < A.NS; s += nwarp) {
     const int l0 = A.segptr[s], l1 = A.segptr[s + 1];
-    for (int l = l0; l < l1; ++l) {
+    for (int l = l0 + lane; l < l1; l += 32) {
       const double xl = xfv(l);
       const double b = A.mf[l] / sp.tau * A.xf_prev[l] + A.Ff[l] + A.FWf[l];
       const double rv = b - frow<L>(A, l, xl, xm, xfv);
@@ -1193,8 +1265,9 @@ __global__ void __launch_bounds__(CT) frac_coupled_kernel(const __grid_constant_
       acc[0] += b * b;
       acc[1] += rv * rv;
     }
-    line_apply(l0, l1, A.llo, A.lcp, A.ldinv, A.rf, A.zf);
-    for (int l = l0; l < l1; ++l) acc[2] += A.rf[l] * A.zf[l];
+    __syncwarp();
+    line_apply_warp(l0, l1, A.llo, A.lcp, A.ldinv, A.rf, A.zf);
+    for (int l = l0 + lane; l < l1; l += 32) acc[2] += A.rf[l] * A.zf[l];
   }
   cstore<3>(acc, A.partials, 0);
   if (!grid_barrier(A.bar)) return;
@@ -1250,16 +1323,17 @@ __global__ void __launch_bounds__(CT) frac_coupled_kernel(const __grid_constant_
         d2[0] += rv * rv;
         d2[1] += rv * zv;
       }
-    for (long long s = gt; s < A.NS; s += gs) {
+    for (long long s = gwarp; s < A.NS; s += nwarp) {
       const int l0 = A.segptr[s], l1 = A.segptr[s + 1];
-      for (int l = l0; l < l1; ++l) {
+      for (int l = l0 + lane; l < l1; l += 32) {
         A.xf[l] = __ldcg(A.xf + l) + al * __ldcg(A.Pf[cur ^ 1] + l);
         const double rv = __ldcg(A.rf + l) - al * __ldcg(A.qf + l);
         A.rf[l] = rv;
         d2[0] += rv * rv;
       }
-      line_apply(l0, l1, A.llo, A.lcp, A.ldinv, A.rf, A.zf);
-      for (int l = l0; l < l1; ++l) d2[1] += A.rf[l] * A.zf[l];
+      __syncwarp();
+      line_apply_warp(l0, l1, A.llo, A.lcp, A.ldinv, A.rf, A.zf);
+      for (int l = l0 + lane; l < l1; l += 32) d2[1] += A.rf[l] * A.zf[l];
     }
     cstore<2>(d2, A.partials, slot);
     if (!grid_barrier(A.bar)) return;
@@ -1408,7 +1482,7 @@ mc_status coupled_step(mc_frac* f, mc_stats* st) {
     if (falloc(f, (void**)&f->cpart, (size_t)2 * CQ * f->cblocks * sizeof(double)) != cudaSuccess ||
         falloc(f, (void**)&f->cbar, 96 * sizeof(unsigned)) != cudaSuccess ||
         falloc(f, (void**)&f->hidx, (size_t)ctx->Np * sizeof(int)) != cudaSuccess ||
-        falloc(f, (void**)&f->Pf2, (size_t)f->P * sizeof(double)) != cudaSuccess)
+        (!f->Pf2 && falloc(f, (void**)&f->Pf2, (size_t)f->P * sizeof(double)) != cudaSuccess))
       return ferr(f, MC_E_ALLOC, "coupled fracture buffers");
     if (cudaMemsetAsync(f->hidx, 0xff, (size_t)ctx->Np * sizeof(int), s) != cudaSuccess)
       return ferr(f, MC_E_CUDA, "hidx");
@@ -1476,6 +1550,170 @@ mc_status coupled_step(mc_frac* f, mc_stats* st) {
   st->rel_residual[0] = rel;
   if (ss[0] != 0)
     return ferr(f, (mc_status)ss[0], std::string("coupled fracture solve: ") + mc_status_string((mc_status)ss[0]));
+  return MC_OK;
+}
+
+
+// ------------------------------------------ fracture solve over the grid ---
+// The fracture system of the decoupled schemes (Eq. app-md's fracture rows,
+// the matrix state lagged or current as the scheme says) for large networks:
+// the same line-preconditioned PCG as frac_solve_kernel (operator, line
+// blocks, stopping test, constant-mode correction), spread over a cooperative
+// grid. Pieces are grid-strided for the operator; segments go one per warp
+// for the line blocks, together with the x and r updates of their pieces, so
+// that each warp's line solve reads only the residuals it wrote. P_new = z +
+// beta P_old is formed on the fly where the operator reads it (two P
+// buffers): two grid reductions per iteration, summed in a fixed CTA order.
+struct FracGridArgs {
+  FracSolve S;
+  double* P2;        // second search-direction buffer
+  double* partials;  // [2][CQ][gridDim.x]
+  GridBar bar;
+};
+
+__global__ void __launch_bounds__(CT) frac_solve_grid_kernel(const __grid_constant__ FracGridArgs G) {
+  const FracSolve& A = G.S;
+  const int P = A.P;
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gs = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const long long gwarp = gt >> 5, nwarp = gs >> 5;
+  // b and r = b - A x (flux form) by segment, then z = M^-1 r of the segment;
+  // b kept in xb for the constant-mode correction
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long sg = gwarp; sg < A.NS; sg += nwarp) {
+    const int l0 = A.segptr[sg], l1 = A.segptr[sg + 1];
+    for (int l = l0 + lane; l < l1; l += 32) {
+      double b = A.mf[l] / A.tau * A.xprev[l] + A.Ff[l] + A.FWf[l];
+      for (int a = 0; a < A.L; ++a) b += A.q[a][l] * A.pm[a][A.hostp[l]];
+      const double rv = b - frac_flux(A, A.x, l, A.x[l]);
+      A.r[l] = rv;
+      A.xb[l] = b;
+      A.p[l] = 0.0;
+      acc[0] += b * b;
+      acc[1] += rv * rv;
+    }
+    __syncwarp();
+    line_apply_warp(l0, l1, A.llo, A.lcp, A.ldinv, A.r, A.z);
+    for (int l = l0 + lane; l < l1; l += 32) acc[2] += __ldcg(A.r + l) * __ldcg(A.z + l);
+  }
+  cstore<3>(acc, G.partials, 0);
+  if (!grid_barrier(G.bar)) return;
+  double t3[3];
+  ctotal<3>(G.partials, 0, t3);
+  const double bb = t3[0];
+  double rr = t3[1], rz = t3[2];
+  const double tol2 = A.rtol * A.rtol;
+  double beta = 0.0;
+  int it = 0, cur = 0, slot = 1, status = 0;
+  while (rr > tol2 * bb) {
+    if (it >= A.max_iter) { status = MC_E_NOCONV; break; }
+    // ---- P_new = z + beta P_old (stored), q = A P_new, <P_new, q> ----------
+    const double bt = beta;
+    const double* Po = cur ? G.P2 : A.p;
+    double* Pn = cur ? A.p : G.P2;
+    double pq[1] = {0.0};
+    for (long long l = gt; l < P; l += gs) {
+      const double pc = fma(bt, __ldcg(Po + l), __ldcg(A.z + l));
+      double v = A.dcf[l] * pc;
+      for (int e = A.rowptr[l]; e < A.rowptr[l + 1]; ++e) {
+        const int nb = A.col[e];
+        v += A.T[e] * (pc - fma(bt, __ldcg(Po + nb), __ldcg(A.z + nb)));
+      }
+      Pn[l] = pc;
+      A.qv[l] = v;
+      pq[0] = fma(pc, v, pq[0]);
+    }
+    cstore<1>(pq, G.partials, slot);
+    if (!grid_barrier(G.bar)) return;
+    double pqt[1];
+    ctotal<1>(G.partials, slot, pqt);
+    slot ^= 1;
+    if (!(pqt[0] > 0.0) || !isfinite(pqt[0])) { status = MC_E_BREAKDOWN; break; }
+    const double al = rz / pqt[0];
+    // ---- x += al P, r -= al q, z = M^-1 r by segment, (r, r), (r, z) ---------
+    double d2[2] = {0.0, 0.0};
+    for (long long sg = gwarp; sg < A.NS; sg += nwarp) {
+      const int l0 = A.segptr[sg], l1 = A.segptr[sg + 1];
+      for (int l = l0 + lane; l < l1; l += 32) {
+        A.x[l] = __ldcg(A.x + l) + al * __ldcg(Pn + l);
+        const double rv = __ldcg(A.r + l) - al * __ldcg(A.qv + l);
+        A.r[l] = rv;
+        d2[0] += rv * rv;
+      }
+      __syncwarp();
+      line_apply_warp(l0, l1, A.llo, A.lcp, A.ldinv, A.r, A.z);
+      for (int l = l0 + lane; l < l1; l += 32) d2[1] += __ldcg(A.r + l) * __ldcg(A.z + l);
+    }
+    cstore<2>(d2, G.partials, slot);
+    if (!grid_barrier(G.bar)) return;
+    double t2[2];
+    ctotal<2>(G.partials, slot, t2);
+    slot ^= 1;
+    ++it;
+    rr = t2[0];
+    if (!isfinite(rr)) { status = MC_E_BREAKDOWN; break; }
+    beta = t2[1] / rz;
+    rz = t2[1];
+    cur ^= 1;
+  }
+  // ---- constant-mode correction: c = 1^T (b - A x) / 1^T dcf ---------------
+  double cs[2] = {0.0, 0.0};
+  if (status == 0)
+    for (long long l = gt; l < P; l += gs) {
+      cs[0] += __ldcg(A.xb + l) - A.dcf[l] * __ldcg(A.x + l);
+      cs[1] += A.dcf[l];
+    }
+  cstore<2>(cs, G.partials, slot);
+  if (!grid_barrier(G.bar)) return;
+  double ct[2];
+  ctotal<2>(G.partials, slot, ct);
+  if (status == 0) {
+    const double c = ct[1] > 0.0 ? ct[0] / ct[1] : 0.0;
+    if (isfinite(c))
+      for (long long l = gt; l < P; l += gs) A.x[l] = __ldcg(A.x + l) + c;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (status) atomicCAS(A.stat, 0, status);
+    A.stat[1] += it;
+    *A.relres = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+  }
+}
+
+// Launch of the grid fracture solve: CTAs enough for one segment per warp and
+// about eight pieces per thread, at most the co-resident count.
+mc_status frac_solve_grid(mc_frac* f, const FracSolve& S) {
+  mc_ctx* ctx = f->ctx;
+  cudaStream_t s = ctx->stream;
+  if (!f->gpart) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (void*)frac_solve_grid_kernel, CT, 0) !=
+            cudaSuccess ||
+        per < 1)
+      return ferr(f, MC_E_CUDA, "grid fracture kernel occupancy");
+    f->gcap = per * ctx->num_sms;
+    const long long want = std::max<long long>((f->NS + CT / 32 - 1) / (CT / 32), ((long long)f->P + 8 * CT - 1) / (8 * CT));
+    f->gblocks = (int)std::max<long long>(1, std::min<long long>(want, f->gcap));
+    if (falloc(f, (void**)&f->gpart, (size_t)2 * CQ * f->gblocks * sizeof(double)) != cudaSuccess ||
+        falloc(f, (void**)&f->gbar, 96 * sizeof(unsigned)) != cudaSuccess)
+      return ferr(f, MC_E_ALLOC, "grid fracture buffers");
+    if (!f->Pf2 && falloc(f, (void**)&f->Pf2, (size_t)f->P * sizeof(double)) != cudaSuccess)
+      return ferr(f, MC_E_ALLOC, "grid fracture buffers");
+  }
+  FracGridArgs G{};
+  G.S = S;
+  G.P2 = f->Pf2;
+  G.partials = f->gpart;
+  G.bar.count = reinterpret_cast<unsigned long long*>(f->gbar);
+  G.bar.abort_word = f->gbar + 64;
+  G.bar.status = f->dstat;
+  G.bar.spin_limit = ctx->opts.spin_limit;
+  if (cudaMemsetAsync(f->gbar, 0, 96 * sizeof(unsigned), s) != cudaSuccess)
+    return ferr(f, MC_E_CUDA, "memset");
+  void* args[] = {&G};
+  if (cudaLaunchCooperativeKernel((void*)frac_solve_grid_kernel, dim3(f->gblocks), dim3(CT), args, 0, s) !=
+      cudaSuccess)
+    return ferr(f, MC_E_CUDA, "grid fracture launch");
   return MC_OK;
 }
 

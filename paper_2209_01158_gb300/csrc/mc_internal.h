@@ -67,9 +67,10 @@ struct StepParams {
   double* w[2][MCL];
   double* pd[MCL];
   int single_pass;
-  // two-level preconditioner (decoupled FP64 path; two_level = 0: Jacobi)
+  // two-level preconditioner (FP64 path; two_level = 0: Jacobi)
   int two_level;
   int nc;                          // coarse unknowns per continuum (stencil tiles)
+  int tl_full;                     // coupled: one (L nc)^2 coarse operator in Ainv[0]
   const double* Ainv[MCL];         // nc x nc inverse of the coarse operator
   double* gsum[MCL];               // P^T r (tile sums)
   double* ccor[MCL];               // coarse correction A_c^-1 P^T r
@@ -187,6 +188,9 @@ struct mc_ctx {
   unsigned* tl_bar = nullptr;
   int tl_nc = 0;
   int tl_ready = 0;
+  double* tl_Afull = nullptr;      // coupled: (L nc)^2 inverse of the Galerkin coarse operator
+  double* tl_work_full = nullptr;
+  int tl_full_ready = 0;
   int maxb = 0;                    // CTAs the partials buffer is sized for
   // precision form (allocated on first use)
   float* r32[MCL] = {};
@@ -235,6 +239,9 @@ cudaError_t mc_gj_invert(double* M, int n, double* work, unsigned* bar, int* sta
 // of continuum a on the 64 x 16 stencil tiles (P = tile indicators), dense
 // nc x nc, assembled into Ac (overwritten).
 cudaError_t mc_launch_coarse_assemble(const mc_ctx* ctx, int a, double* Ac);
+// The coupled scheme's Galerkin coarse operator P^T A P with P = blockdiag(P_a):
+// (L nc)^2, the per-continuum blocks above plus the exchange blocks.
+cudaError_t mc_launch_coarse_assemble_coupled(const mc_ctx* ctx, double* Ac);
 int mc_step_tiles(int nx, int ny);
 
 // Maximum co-resident CTAs for the step kernel of this L (cooperative grid).

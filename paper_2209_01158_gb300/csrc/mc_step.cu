@@ -223,6 +223,33 @@ __device__ void coarse_correct(const StepParams& sp, unsigned act, Smem& sm, dou
   const long long gw = ((long long)blockIdx.x * NT + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * NT) >> 5;
   double* sg = sm.box;  // P^T r staged in the idle TMA ring
+  if (sp.tl_full) {
+    // coupled: one Galerkin system over all continua (exchange blocks included)
+#pragma unroll
+    for (int a = 0; a < L; ++a) gc[a] = 0.0;
+    const int n = L * nc;
+    for (int J = threadIdx.x; J < n; J += NT) {
+      const int a = J / nc;
+      sg[J] = ldc(sp.gsum[a] + (J - a * nc));
+    }
+    __syncthreads();
+    const double* Ai = sp.Ainv[0];
+    for (long long R = gw; R < n; R += nw) {
+      const double* row = Ai + R * n;
+      double v = 0.0;
+      for (int J = lane; J < n; J += 32) v = fma(ldr(row + J), sg[J], v);
+      v = warp_sum(v);
+      if (lane == 0) {
+        const int a = (int)(R / nc);
+        sp.ccor[a][R - (long long)a * nc] = v;
+#pragma unroll
+        for (int k = 0; k < L; ++k)
+          if (k == a) gc[k] = fma(sg[R], v, gc[k]);
+      }
+    }
+    __syncthreads();
+    return;
+  }
 #pragma unroll
   for (int a = 0; a < L; ++a) {
     gc[a] = 0.0;
@@ -328,7 +355,11 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
   int cur = 0;
   int slot = 1;
   bool ok = true;
-  constexpr bool TL = !COUPLED && TLV;
+  // Two-level: the coarse correction of every continuum. The coupled scheme
+  // takes the coarse space blockdiag(P_a) with the Galerkin operator P^T A P
+  // of the coupled matrix (exchange blocks included, sp.tl_full), its (r, z)
+  // the sum over the continua.
+  constexpr bool TL = TLV;
   if (TL && active) {
     // z_0 = D^-1 r_0 + P c_0: the coarse term, and its share of (r_0, z_0)
     tile_rsums<L>(sp, active, sm);
@@ -339,9 +370,12 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
     if (!grid_sync(sp)) return false;
     grid_totals<L>(sp.partials, slot, sm.res);
     slot ^= 1;
-    if (tid == 0)
+    if (tid == 0) {
+      double gsum = 0.0;
+      for (int a = 0; a < L; ++a) gsum += sm.res[a];
       for (int a = 0; a < L; ++a)
-        if (active & (1u << a)) S.rz[a] += sm.res[a];
+        if (active & (1u << a)) S.rz[a] += COUPLED ? gsum : sm.res[a];
+    }
     __syncthreads();
   }
 
@@ -447,11 +481,14 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       phb ^= 1u << s;
       pend &= ~(1u << s);
       if (TL) {
-        // c of this tile and of its 8 neighbours (0 outside the tile grid)
-        if (tid < 9) {
-          const int cx = tt % sp.tiles_x + tid % 3 - 1, cy = tt / sp.tiles_x + tid / 3 - 1;
+        // c of this tile and of its 8 neighbours (0 outside the tile grid),
+        // for every continuum of the tile
+        if (tid < 9 * NL) {
+          const int l = tid / 9, kk = tid - 9 * l;
+          const int a = COUPLED ? l : a0;
+          const int cx = tt % sp.tiles_x + kk % 3 - 1, cy = tt / sp.tiles_x + kk / 3 - 1;
           sm.cn[tid] = (cx >= 0 && cx < sp.tiles_x && cy >= 0 && cy < sp.tiles_y)
-                           ? ldc(sp.ccor[a0] + cy * sp.tiles_x + cx)
+                           ? ldc(sp.ccor[a] + cy * sp.tiles_x + cx)
                            : 0.0;
         }
         __syncthreads();
@@ -469,7 +506,8 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
           const int ry = e / PX, rx = e - ry * PX;
           const int bidx = ry * BX + rx + 1;
           double zc = bz[bidx];
-          if (TL) zc += sm.cn[(ry == 0 ? 0 : (ry == BY - 1 ? 6 : 3)) + (rx == 0 ? 0 : (rx == PX - 1 ? 2 : 1))];
+          if (TL)
+            zc += sm.cn[9 * l + (ry == 0 ? 0 : (ry == BY - 1 ? 6 : 3)) + (rx == 0 ? 0 : (rx == PX - 1 ? 2 : 1))];
           pn[e] = fma(bt, bp[bidx], zc);
         }
       }
@@ -554,7 +592,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       // tile by tile (same hand-out as phase A), so that P^T r of every tile
       // is summed inside one CTA
       const int lane = tid & 31, warp = tid >> 5;
-      for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+      for (int t = blockIdx.x; t < nact * tiles; t += gridDim.x) {
         const int w = t / tiles, tt = t - w * tiles;
         int a0 = 0;
 #pragma unroll
@@ -669,13 +707,16 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       if (!grid_sync(sp)) { ok = false; break; }
       grid_totals<L>(sp.partials, slot, sm.res);
       slot ^= 1;
-      if (tid == 0)
+      if (tid == 0) {
+        double gsum = 0.0;
+        for (int a = 0; a < L; ++a) gsum += sm.res[a];
         for (int a = 0; a < L; ++a)
           if (active & (1u << a)) {
-            const double rzn = S.rzl[a] + sm.res[a];
+            const double rzn = S.rzl[a] + (COUPLED ? gsum : sm.res[a]);
             S.beta[a] = rzn / S.rz[a];
             S.rz[a] = rzn;
           }
+      }
       __syncthreads();
     }
     cur ^= 1;
@@ -1645,8 +1686,8 @@ __device__ bool pcg_solve_scaled(const StepParams& sp, const TmaMaps& maps, unsi
   return false;
 }
 
-// MODE 0: Jacobi PCG, flux-form stencil; 1: two-level preconditioner
-// (decoupled); 2: Jacobi PCG in scaled variables.
+// MODE 0: Jacobi PCG, flux-form stencil; 1: two-level preconditioner; 2:
+// Jacobi PCG in scaled variables, two passes; 3: the same, single pass.
 template <int L, bool COUPLED, int MODE>
 __global__ void __launch_bounds__(NT, 1)
     step_kernel(const __grid_constant__ StepParams sp, const __grid_constant__ TmaMaps maps) {
@@ -1659,7 +1700,7 @@ __global__ void __launch_bounds__(NT, 1)
   unsigned char* smem_base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   __shared__ Scal64 s_scal;
-  __shared__ double s_cn[9];
+  __shared__ double s_cn[9 * MCL];
   Smem sm;
   sm.sc = &s_scal;
   sm.cn = s_cn;
@@ -1686,7 +1727,7 @@ __global__ void __launch_bounds__(NT, 1)
       for (long long i = gtid; i < Np; i += gstride) sp.pprev[a][i] = ldc(sp.p[a] + i);
     if (COUPLED) {
       if (MODE >= 2) ok = pcg_solve_scaled<L, true, MODE == 3>(sp, maps, (1u << L) - 1u, sm, phb);
-      else ok = pcg_solve<L, true, false>(sp, maps, (1u << L) - 1u, sm, phb);
+      else ok = pcg_solve<L, true, MODE == 1>(sp, maps, (1u << L) - 1u, sm, phb);
     } else if (sp.scheme == MC_SCHEME_D) {
       if (MODE >= 2) ok = pcg_solve_scaled<L, false, MODE == 3>(sp, maps, (1u << L) - 1u, sm, phb);
       else ok = pcg_solve<L, false, MODE == 1>(sp, maps, (1u << L) - 1u, sm, phb);
@@ -1765,7 +1806,14 @@ KInfo info() {
 
 template <int L>
 KInfo pick_l(bool coupled, int mode) {
-  if (coupled) return mode == 3 ? info<L, true, 3>() : (mode == 2 ? info<L, true, 2>() : info<L, true, 0>());
+  if (coupled) {
+    switch (mode) {
+      case 1: return info<L, true, 1>();
+      case 2: return info<L, true, 2>();
+      case 3: return info<L, true, 3>();
+      default: return info<L, true, 0>();
+    }
+  }
   switch (mode) {
     case 1: return info<L, false, 1>();
     case 2: return info<L, false, 2>();
@@ -1774,7 +1822,7 @@ KInfo pick_l(bool coupled, int mode) {
   }
 }
 
-// mode: 0 flux-form Jacobi, 1 two-level (decoupled only), 2 scaled Jacobi
+// mode: 0 flux-form Jacobi, 1 two-level, 2 scaled Jacobi
 // (two phases, two reductions per iteration), 3 scaled Jacobi single-pass
 KInfo pick(int L, bool coupled, int mode = 0) {
   switch (L) {
@@ -1800,7 +1848,7 @@ int max_blocks_for(KInfo k, int threads, int num_sms) {
 // symmetric). Ac must be zero on entry.
 __global__ void coarse_assemble_kernel(int nx, int ny, int pitch, int tiles_x, int tiles_y,
                                        const double* TE, const double* TN, const double* diagc,
-                                       double diagc_const, double* Ac) {
+                                       double diagc_const, double* Ac, long long ld) {
   const int nc = tiles_x * tiles_y;
   for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
     const int x0 = (I % tiles_x) * TX, y0 = (I / tiles_x) * TY;
@@ -1816,12 +1864,39 @@ __global__ void coarse_assemble_kernel(int nx, int ny, int pitch, int tiles_x, i
       if (y1 < ny) tn += TN[(long long)(y1 - 1) * pitch + x];
       if (y0 > 0) ts += TN[(long long)(y0 - 1) * pitch + x];
     }
-    double* row = Ac + (long long)I * nc;
+    double* row = Ac + (long long)I * ld;
     row[I] = d + te + tw + tn + ts;
     if (x1 < nx) row[I + 1] = -te;
     if (x0 > 0) row[I - 1] = -tw;
     if (y1 < ny) row[I + tiles_x] = -tn;
     if (y0 > 0) row[I - tiles_x] = -ts;
+  }
+}
+
+// Exchange blocks of the coupled Galerkin coarse operator P^T A P, P =
+// blockdiag(P_a): entry ((a, I), (b, I)) = -(sum over the cells of tile I of
+// q_ab), the same cells in the same order for (a, b) and (b, a), so the
+// operator stays exactly symmetric. The diagonal blocks already carry +sum_b
+// q_ab through diagc. Ac holds the (L nc)^2 matrix, row stride ld.
+struct ExchArgs {
+  const double* qcell[MCL][MCL];
+  double qconst[MCL][MCL];
+};
+
+__global__ void coarse_exchange_kernel(int nx, int ny, int pitch, int tiles_x, int nc, int L,
+                                       const __grid_constant__ ExchArgs q, double* Ac, long long ld) {
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+    const int x0 = (I % tiles_x) * TX, y0 = (I / tiles_x) * TY;
+    const int x1 = min(x0 + TX, nx), y1 = min(y0 + TY, ny);
+    for (int a = 0; a < L; ++a)
+      for (int b = a + 1; b < L; ++b) {
+        const double* qc = q.qcell[a][b];
+        double sq = 0.0;
+        for (int y = y0; y < y1; ++y)
+          for (int x = x0; x < x1; ++x) sq += qc ? qc[(long long)y * pitch + x] : q.qconst[a][b];
+        Ac[((long long)a * nc + I) * ld + (long long)b * nc + I] = -sq;
+        Ac[((long long)b * nc + I) * ld + (long long)a * nc + I] = -sq;
+      }
   }
 }
 
@@ -1840,13 +1915,39 @@ cudaError_t mc_launch_coarse_assemble(const mc_ctx* ctx, int a, double* Ac) {
   const int blocks = (int)((nc + 127) / 128);
   coarse_assemble_kernel<<<blocks, 128, 0, ctx->stream>>>(ctx->nx, ctx->ny, ctx->pitch, tx, ty,
                                                           ctx->TE[a], ctx->TN[a], ctx->diagc[a],
-                                                          dconst, Ac);
+                                                          dconst, Ac, nc);
+  return cudaGetLastError();
+}
+
+cudaError_t mc_launch_coarse_assemble_coupled(const mc_ctx* ctx, double* Ac) {
+  const int tx = (ctx->nx + TX - 1) / TX, ty = (ctx->ny + TY - 1) / TY;
+  const long long nc = (long long)tx * ty;
+  const long long n = (long long)ctx->L * nc;
+  cudaError_t e = cudaMemsetAsync(Ac, 0, (size_t)(n * n) * sizeof(double), ctx->stream);
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)((nc + 127) / 128);
+  ExchArgs q{};
+  for (int a = 0; a < ctx->L; ++a) {
+    double dconst = ctx->c[a] * ctx->h * ctx->h / ctx->tau;
+    for (int b = 0; b < ctx->L; ++b) {
+      if (b != a) dconst += ctx->sigma[a][b] * ctx->h * ctx->h;
+      q.qcell[a][b] = ctx->qcell[a][b];
+      q.qconst[a][b] = ctx->sigma[a][b] * ctx->h * ctx->h;
+    }
+    coarse_assemble_kernel<<<blocks, 128, 0, ctx->stream>>>(ctx->nx, ctx->ny, ctx->pitch, tx, ty,
+                                                            ctx->TE[a], ctx->TN[a], ctx->diagc[a], dconst,
+                                                            Ac + (a * nc) * n + a * nc, n);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  coarse_exchange_kernel<<<blocks, 128, 0, ctx->stream>>>(ctx->nx, ctx->ny, ctx->pitch, tx, (int)nc, ctx->L, q,
+                                                          Ac, n);
   return cudaGetLastError();
 }
 
 int mc_step_max_blocks(int L, int threads, int num_sms) {
   int m = max_blocks_for(pick(L, true), threads, num_sms);
-  for (int mode = 2; mode < 4; ++mode) {
+  for (int mode = 1; mode < 4; ++mode) {
     const int c = max_blocks_for(pick(L, true, mode), threads, num_sms);
     if (c < m) m = c;
   }

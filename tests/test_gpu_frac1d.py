@@ -5,7 +5,9 @@ The mesh the library builds must match the oracle's piece by piece (count,
 host cells exactly; lengths and midpoints to roundoff). The D-, L-, U- and
 coupled steps must match the oracle's exact solves at the FP64 bar: relative
 L2 over all matrix cells and pieces jointly, and the elementwise error
-max|p - p_ref| / max|p_ref|, both <= 1e-10 at rtol 1e-12.
+max|p - p_ref| / max|p_ref|, both <= 1e-10 at rtol 1e-12. Networks below
+8192 pieces take the one-CTA fracture solve, larger ones the grid solve; the
+cases cover both.
 """
 
 import numpy as np
@@ -67,6 +69,9 @@ STEP_CASES = [
     ("paper3c_60", lambda: mi.fracture1d(2, n=60), 4),
     ("src_L1_72", lambda: mi.fracture1d_sources(1, n=72, nsteps=4), 4),
     ("src_L2_66", lambda: mi.fracture1d_sources(2, n=66, nsteps=4), 4),
+    # networks of 8749 and 13184 pieces: the fracture solve runs over the grid
+    ("src_L1_200", lambda: mi.fracture1d_sources(1, n=200, nsteps=3), 3),
+    ("src_L2_256", lambda: mi.fracture1d_sources(2, n=256, nsteps=3), 3),
 ]
 
 

@@ -1,10 +1,11 @@
 """GPU parity of the two-level preconditioner option (Jacobi plus a Galerkin
-coarse correction on the 64 x 16 stencil tiles) of the FP64 decoupled path.
+coarse correction on the 64 x 16 stencil tiles) of the FP64 path.
 
 The preconditioner changes only the Krylov iteration, so the bars are the
 FP64 path's own: rel-L2 <= 1e-10 against the oracle at rtol 1e-12, on
 ragged grids (not multiples of the tile), with per-cell exchange and wells,
-for the D-, L- and U-schemes; and fewer iterations than Jacobi.
+for the D-, L- and U-schemes and the coupled scheme (block-diagonal coarse
+space, one per continuum); and fewer iterations than Jacobi.
 """
 
 import numpy as np
@@ -37,7 +38,7 @@ def run(mc, w, scheme, nsteps, precond, rtol=1e-12):
     return p, st
 
 
-@pytest.mark.parametrize("scheme", ["D", "L", "U"])
+@pytest.mark.parametrize("scheme", ["D", "L", "U", "coupled"])
 @pytest.mark.parametrize("case", ["triple_100", "fracture_72_L3", "paper3C_66", "dual_64"])
 def test_two_level_matches_oracle(mc, case, scheme):
     w = {"triple_100": lambda: mi.triple_1024(n=100),
@@ -60,14 +61,21 @@ def test_two_level_cuts_iterations(mc):
     assert metrics.rel_l2(ref, p) <= FP64_TOL
 
 
+def test_two_level_cuts_coupled_iterations(mc):
+    w = mi.triple_1024(n=256)
+    _, sj = run(mc, w, "coupled", 3, mc.N.MC_PRECOND_JACOBI)
+    p, st = run(mc, w, "coupled", 3, mc.N.MC_PRECOND_TWO_LEVEL)
+    assert st["iters"][0] < 0.5 * sj["iters"][0], (st["iters"], sj["iters"])
+    ref = from_workload(w).run(w.p0, w.F, 3, "coupled")
+    assert metrics.rel_l2(ref, p) <= FP64_TOL
+
+
 def test_two_level_refused_where_it_does_not_apply(mc):
     w = mi.dual_64(n=32)
     o = mc.mc_default_opts()
     o.precond = mc.N.MC_PRECOND_TWO_LEVEL
-    ctx = mc.Context.from_workload(w, opts=o)
-    assert ctx.step("coupled", 1, check=False)["return"] == mc.N.MC_E_ARG
     o.precision = 1
-    ctx.set_opts(o)
+    ctx = mc.Context.from_workload(w, opts=o)
     assert ctx.step("D", 1, check=False)["return"] == mc.N.MC_E_ARG
     ctx.close()
     # 64 x 16 tiles: a 2112 x 1024 grid has 33 x 64 = 2112 tiles > 2048
@@ -76,4 +84,10 @@ def test_two_level_refused_where_it_does_not_apply(mc):
     k = [np.ones(2112 * 1024)]
     ctx = mc.Context(2112, 1024, k, [1.0], None, None, 0.01, o)
     assert ctx.step("D", 1, check=False)["return"] == mc.N.MC_E_ARG
+    ctx.close()
+    # coupled: L x tiles = 3 x (16 x 88) = 4224 > MC_TWO_LEVEL_MAX_COUPLED; D still runs
+    k = [np.ones(1024 * 1408)] * 3
+    ctx = mc.Context(1024, 1408, k, [1.0, 1.0, 1.0], np.full((3, 3), 0.1), None, 0.01, o)
+    assert ctx.step("coupled", 1, check=False)["return"] == mc.N.MC_E_ARG
+    assert ctx.step("D", 1, check=False)["return"] == mc.N.MC_OK
     ctx.close()
