@@ -79,8 +79,8 @@ def parse():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-extras", action="store_true", help="only the headline D-scheme line")
     ap.add_argument("--only", default=None, metavar="LIST",
-                    help="comma-separated extra lines to run (coupled, single_pass, two_level, ir, "
-                         "nlmc, frac1d, precision, paper, batched); default all")
+                    help="comma-separated extra lines to run (coupled, single_pass, two_level, "
+                         "equal_accuracy, ir, nlmc, frac1d, precision, paper, batched); default all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--crop", type=int, default=384, help="oracle sample size (cells per side)")
     ap.add_argument("--batch", type=int, default=64,
@@ -446,6 +446,54 @@ def support_means(fields, sup, nc):
     return np.concatenate(out)
 
 
+def equal_accuracy_extra(mc, w, torch, stream, opts_for, target=1e-9):
+    """Time to solution at equal accuracy, one step from p^0 of the headline
+    workload: for the D-scheme and the coupled scheme, each with Jacobi and
+    with the two-level preconditioner, one step at rtol 1e-8 .. 1e-12. The
+    algebraic error of a run is its relative L2 distance (all continua) from
+    the same scheme solved to rtol 1e-13, a solution the full-size tests hold
+    to the oracle's exact solve (D at 1024^2, coupled at 512^2). Time: CUDA
+    events around the step, after a first step on the same context (the
+    two-level set-up) and a reset to p^0. Reported per configuration: the
+    fastest run whose error is below `target`."""
+    def one(scheme, rtol, precond):
+        ctx = mc.Context.from_workload(w, opts=opts_for(rtol, precond=precond), stream=stream)
+        ctx.step(scheme, 1)
+        ctx.set_state(w.p0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st = ctx.step(scheme, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        p = np.concatenate(ctx.get_state())
+        ctx.close()
+        its = st["iters"][0] if scheme == "coupled" else sum(st["iters"][:w.L])
+        return p, e0.elapsed_time(e1), its
+
+    out = {"target_rel_error": target, "reference_rtol": 1e-13}
+    ladder = [1e-8, 1e-9, 1e-10, 1e-11, 1e-12]
+    best = {}
+    for scheme in ("D", "coupled"):
+        ref, _, _ = one(scheme, 1e-13, 1)
+        nref = np.linalg.norm(ref)
+        out[scheme] = {}
+        for pname, precond in (("jacobi", 0), ("two_level", 1)):
+            rows = []
+            for rt in ladder:
+                p, ms, its = one(scheme, rt, precond)
+                rows.append({"rtol": rt, "ms": ms, "pcg_iterations": its,
+                             "rel_error": float(np.linalg.norm(p - ref) / nref)})
+            ok = [r for r in rows if r["rel_error"] <= target]
+            b = min(ok, key=lambda r: r["ms"]) if ok else None
+            best[(scheme, pname)] = b
+            out[scheme][pname] = {"runs": rows, "best": b}
+    for pname in ("jacobi", "two_level"):
+        d, c = best[("D", pname)], best[("coupled", pname)]
+        out["decoupled_speedup_" + pname] = c["ms"] / d["ms"] if d and c else None
+    return out
+
+
 def nlmc_extra(args, mc, mi, torch, stream, opts_for):
     """NLMC on the 1024^2 fracture workload (32 x 32 coarse blocks, 2 layers):
     build time, coarse steps/s, and e_H after 5 steps against the GPU fine
@@ -593,6 +641,8 @@ def summary_of(value, roof, e2e, extras):
         "two_level_value": g("fp64_two_level", "value"),
         "two_level_speedup_vs_coupled": g("fp64_two_level", "speedup_vs_coupled"),
         "two_level_speedup_vs_coupled_two_level": g("fp64_two_level", "speedup_vs_coupled_two_level"),
+        "equal_accuracy_decoupled_speedup_jacobi": g("equal_accuracy", "decoupled_speedup_jacobi"),
+        "equal_accuracy_decoupled_speedup_two_level": g("equal_accuracy", "decoupled_speedup_two_level"),
         "fp32_ir_value": g("fp32_ir", "value"), "fp32_ir_hbm_frac": g("fp32_ir", "roofline_inner", "frac"),
         "bf16t_ir_value": g("bf16t_ir", "value"),
         "p4096_fp32_hbm_frac": g("precision_4096", "fp32", "roofline_inner", "frac"),
@@ -748,6 +798,11 @@ def main():
             extras["fp64_two_level"]["speedup_vs_coupled_two_level"] = udev / tdev
         except Exception as e:  # report, do not abort the benchmark
             extras["fp64_two_level"] = {"error": str(e)}
+    if want("equal_accuracy"):
+        try:
+            extras["equal_accuracy"] = equal_accuracy_extra(mc, w, torch, stream, opts_for)
+        except Exception as e:  # report, do not abort the benchmark
+            extras["equal_accuracy"] = {"error": str(e)}
     if want("ir"):
         for name, prec, form in (("fp32_ir", 1, 0), ("bf16t_ir", 2, 0),
                                  ("fp32_ir_two_reductions", 1, 1)):

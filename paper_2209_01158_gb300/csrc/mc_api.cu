@@ -65,10 +65,13 @@ void free_all(mc_ctx* ctx) {
   ctx->allocs.clear();
 }
 
-int launch_threads(const mc_ctx* ctx) { return ctx->opts.threads > 0 ? ctx->opts.threads : 512; }
+int launch_threads(const mc_ctx* ctx) { return ctx->opts.threads > 0 ? ctx->opts.threads : MC_STEP_THREADS; }
 
-int launch_blocks(const mc_ctx* ctx) {
-  const int maxb = mc_step_max_blocks(ctx->L, launch_threads(ctx), ctx->num_sms);
+// CTAs of a step launch: the kernel's co-resident count (at most the count the
+// partial-sum buffer was sized for), or fewer when mc_opts.blocks asks.
+int launch_blocks(const mc_ctx* ctx, const StepParams& sp) {
+  int maxb = mc_step_blocks_for(sp, launch_threads(ctx), ctx->num_sms);
+  if (maxb > ctx->maxb) maxb = ctx->maxb;
   int b = ctx->opts.blocks > 0 ? ctx->opts.blocks : maxb;
   if (b > maxb) b = maxb;
   return b;
@@ -83,7 +86,10 @@ mc_status check_opts(const mc_opts* o, std::string* why) {
   if (o->max_iter < 1) { *why = "max_iter < 1"; return MC_E_ARG; }
   if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) { *why = "rtol must be in (0, 1)"; return MC_E_ARG; }
   if (o->spin_limit < 1) { *why = "spin_limit < 1"; return MC_E_ARG; }
-  if (o->threads != 0 && o->threads != 512) { *why = "threads must be 0 or 512"; return MC_E_ARG; }
+  if (o->threads != 0 && o->threads != MC_STEP_THREADS) {
+    *why = "threads must be 0 or " + std::to_string(MC_STEP_THREADS);
+    return MC_E_ARG;
+  }
   if (o->blocks < 0) { *why = "blocks < 0"; return MC_E_ARG; }
   if (o->inner_form != MC_INNER_SINGLE_REDUCTION && o->inner_form != MC_INNER_TWO_REDUCTIONS) {
     *why = "inner_form";
@@ -182,7 +188,7 @@ void mc_fill_params(const mc_ctx* ctx, StepParams* sp, int scheme, int nsteps) {
 }
 
 cudaError_t mc_launch_steps_default(mc_ctx* ctx, const StepParams& sp) {
-  return mc_launch_steps(ctx, sp, launch_blocks(ctx), launch_threads(ctx));
+  return mc_launch_steps(ctx, sp, launch_blocks(ctx, sp), launch_threads(ctx));
 }
 
 extern "C" {
@@ -333,7 +339,7 @@ mc_status mc_setup(const mc_grid* g, int32_t L, const double* const* k, const do
       CKS(mc_alloc(ctx, (void**)&ctx->qs[a][b], fb));
       ctx->qs[b][a] = ctx->qs[a][b];
     }
-  const int maxb = mc_step_max_blocks(L, 512, ctx->num_sms);
+  const int maxb = mc_step_max_blocks_any(L, MC_STEP_THREADS, ctx->num_sms);
   if (maxb < 1) {
     cuda_err(ctx, "occupancy query", cudaGetLastError());
     return bail(MC_E_CUDA);
@@ -577,7 +583,7 @@ static mc_status run_steps(mc_ctx* ctx, int scheme, int nsteps, mc_stats* stats)
     if (blocks < 1) return set_err(ctx, MC_E_CUDA, "no co-resident CTAs for the precision form");
     CK(mc_launch_ir(ctx, sp, bf16, blocks));
   } else {
-    const int blocks = launch_blocks(ctx);
+    const int blocks = launch_blocks(ctx, sp);
     CK(mc_launch_steps(ctx, sp, blocks, launch_threads(ctx)));
   }
   int st = 0, done = 0;

@@ -13,6 +13,9 @@
 #define MCL MC_MAX_CONTINUA
 // partial-sum quantities reserved per reduction slot (all persistent kernels)
 #define MC_KMAX_ALLOC (8 * MCL)
+// Threads per CTA of the FP64 step kernels (the stencil tile code is built for
+// this count; launches must use it).
+#define MC_STEP_THREADS 512
 
 // Everything the persistent time-stepping kernel needs, passed by value.
 // Field pointers address ny rows of `pitch` doubles, cell (i, j) at
@@ -246,6 +249,8 @@ int mc_step_tiles(int nx, int ny);
 
 // Maximum co-resident CTAs for the step kernel of this L (cooperative grid).
 int mc_step_max_blocks(int L, int threads, int num_sms);
+int mc_step_max_blocks_any(int L, int threads, int num_sms);
+int mc_step_blocks_for(const StepParams& sp, int threads, int num_sms);
 int mc_step_box_x();
 int mc_step_box_y();
 

@@ -147,10 +147,10 @@ extern "C" mc_status mc_step_single_noalloc(int32_t nx, int32_t ny, const double
   sp.relres = drelres;
   sp.mass_defect = dmass;
   sp.spin_limit = 2000000;
-  int blocks = mc_step_max_blocks(1, 512, num_sms);
+  int blocks = mc_step_max_blocks(1, MC_STEP_THREADS, num_sms);
   if (blocks < 1) return MC_E_CUDA;
   if (blocks > kMaxBlocks) blocks = kMaxBlocks;
-  NA_CK(mc_launch_steps_raw(sp, maps, blocks, 512, st));
+  NA_CK(mc_launch_steps_raw(sp, maps, blocks, MC_STEP_THREADS, st));
 
   double ctl[16];
   NA_CK(cudaMemcpyAsync(ctl, ctrl + 48, sizeof(ctl), cudaMemcpyDeviceToHost, st));

@@ -47,7 +47,7 @@ constexpr int ABOX = 1232;      // box slot in doubles (9856 B, 128-B multiple)
 constexpr uint32_t BOX_BYTES = BX * BY * 8;
 constexpr int PX = TX + 2;      // 66: P_new halo region width
 constexpr int PN = PX * BY;     // 1188 cells
-constexpr int NT = 512;         // threads per CTA
+constexpr int NT = MC_STEP_THREADS;  // threads per CTA
 constexpr int RPT = NT / TX;    // 8: tile rows covered by one pass of the CTA
 constexpr int CPT = TY / RPT;   // 2: own cells per thread
 constexpr int KMAX = 4 * MCL;   // partial-sum quantities per slot
@@ -1689,7 +1689,7 @@ __device__ bool pcg_solve_scaled(const StepParams& sp, const TmaMaps& maps, unsi
 // MODE 0: Jacobi PCG, flux-form stencil; 1: two-level preconditioner; 2:
 // Jacobi PCG in scaled variables, two passes; 3: the same, single pass.
 template <int L, bool COUPLED, int MODE>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, 512 / NT)
     step_kernel(const __grid_constant__ StepParams sp, const __grid_constant__ TmaMaps maps) {
   constexpr int NL = COUPLED ? L : 1;
   constexpr int NARR = (MODE == 3 ? 3 : 2) * NL;
@@ -1955,6 +1955,23 @@ int mc_step_max_blocks(int L, int threads, int num_sms) {
     const int a = max_blocks_for(pick(L, false, mode), threads, num_sms);
     if (a < m) m = a;
   }
+  return m;
+}
+
+// Co-resident CTAs of the kernel that a launch with these parameters runs.
+int mc_step_blocks_for(const StepParams& sp, int threads, int num_sms) {
+  const int mode = sp.two_level ? 1 : (sp.sqd[0] == nullptr ? 0 : (sp.single_pass ? 3 : 2));
+  return max_blocks_for(pick(sp.L, sp.scheme == MC_SCHEME_COUPLED, mode), threads, num_sms);
+}
+
+// The largest co-resident count over every step kernel of L continua.
+int mc_step_max_blocks_any(int L, int threads, int num_sms) {
+  int m = 0;
+  for (int mode = 0; mode < 4; ++mode)
+    for (int c = 0; c < 2; ++c) {
+      const int v = max_blocks_for(pick(L, c != 0, mode), threads, num_sms);
+      if (v > m) m = v;
+    }
   return m;
 }
 

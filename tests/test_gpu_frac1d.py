@@ -64,24 +64,28 @@ def test_mesh_matches_oracle(mc, name, make):
     ctx.close()
 
 
+# (name, workload, steps[, rtol]); the two large networks solve to rtol 1e-13:
+# at 1e-12 their L- and U-scheme forward error reaches 1.2e-10 elementwise
+# (relative L2 6e-11), the conditioning of the k_f = 1e4 fracture graph.
 STEP_CASES = [
     ("paper2c_60", lambda: mi.fracture1d(1, n=60), 4),
     ("paper3c_60", lambda: mi.fracture1d(2, n=60), 4),
     ("src_L1_72", lambda: mi.fracture1d_sources(1, n=72, nsteps=4), 4),
     ("src_L2_66", lambda: mi.fracture1d_sources(2, n=66, nsteps=4), 4),
     # networks of 8749 and 13184 pieces: the fracture solve runs over the grid
-    ("src_L1_200", lambda: mi.fracture1d_sources(1, n=200, nsteps=3), 3),
-    ("src_L2_256", lambda: mi.fracture1d_sources(2, n=256, nsteps=3), 3),
+    ("src_L1_200", lambda: mi.fracture1d_sources(1, n=200, nsteps=3), 3, 1e-13),
+    ("src_L2_256", lambda: mi.fracture1d_sources(2, n=256, nsteps=3), 3, 1e-13),
 ]
+STEP_CASES = [c if len(c) == 4 else c + (1e-12,) for c in STEP_CASES]
 
 
 @pytest.mark.parametrize("scheme", ["D", "L", "U"])
-@pytest.mark.parametrize("name,make,nsteps", STEP_CASES)
-def test_decoupled_schemes_match_oracle(mc, name, make, nsteps, scheme):
+@pytest.mark.parametrize("name,make,nsteps,rtol", STEP_CASES)
+def test_decoupled_schemes_match_oracle(mc, name, make, nsteps, rtol, scheme):
     w = make()
     o, p0 = oracle_frac(w)
     ref = o.run(p0, w.F, nsteps, scheme)
-    ctx, f = _pair(mc, w)
+    ctx, f = _pair(mc, w, rtol=rtol)
     st = f.step(scheme, nsteps)
     pm, pf = f.get_state()
     f.close()
@@ -91,12 +95,12 @@ def test_decoupled_schemes_match_oracle(mc, name, make, nsteps, scheme):
     assert st["steps_done"] == nsteps and st["iters"][w.L] > 0
 
 
-@pytest.mark.parametrize("name,make,nsteps", STEP_CASES[:3])
-def test_coupled_scheme_matches_oracle(mc, name, make, nsteps):
+@pytest.mark.parametrize("name,make,nsteps,rtol", STEP_CASES[:3])
+def test_coupled_scheme_matches_oracle(mc, name, make, nsteps, rtol):
     w = make()
     o, p0 = oracle_frac(w)
     ref = o.run(p0, w.F, nsteps, "coupled")
-    ctx, f = _pair(mc, w)
+    ctx, f = _pair(mc, w, rtol=rtol)
     st = f.step("coupled", nsteps)
     pm, pf = f.get_state()
     f.close()
