@@ -113,7 +113,7 @@ typedef struct {
                           (default 1e-3) */
   int64_t spin_limit;  /* polls of a grid barrier before MC_E_TIMEOUT */
   int32_t blocks;      /* persistent CTAs (0: one per SM x occupancy) */
-  int32_t threads;     /* threads per CTA (0: default 512) */
+  int32_t threads;     /* threads per CTA of the FP64 step kernels (0: default 256; any other value is MC_E_ARG) */
   int32_t inner_form;  /* MC_INNER_* (IR forms; default single reduction) */
   int32_t fp64_form;   /* MC_FP64_* iteration of the FP64 Jacobi PCG (default
                           two passes) */

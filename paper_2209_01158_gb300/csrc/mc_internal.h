@@ -15,7 +15,7 @@
 #define MC_KMAX_ALLOC (8 * MCL)
 // Threads per CTA of the FP64 step kernels (the stencil tile code is built for
 // this count; launches must use it).
-#define MC_STEP_THREADS 512
+#define MC_STEP_THREADS 256
 
 // Everything the persistent time-stepping kernel needs, passed by value.
 // Field pointers address ny rows of `pitch` doubles, cell (i, j) at

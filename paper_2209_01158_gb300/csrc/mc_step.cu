@@ -48,14 +48,18 @@ constexpr uint32_t BOX_BYTES = BX * BY * 8;
 constexpr int PX = TX + 2;      // 66: P_new halo region width
 constexpr int PN = PX * BY;     // 1188 cells
 constexpr int NT = MC_STEP_THREADS;  // threads per CTA
-constexpr int RPT = NT / TX;    // 8: tile rows covered by one pass of the CTA
-constexpr int CPT = TY / RPT;   // 2: own cells per thread
+constexpr int RPT = NT / TX;    // 4: tile rows covered by one pass of the CTA
+constexpr int CPT = TY / RPT;   // 4: own cells per thread
 constexpr int KMAX = 4 * MCL;   // partial-sum quantities per slot
 
-// TMA pipeline depth: enough boxes in flight per SM to cover the DRAM
-// latency (Little's law: ~64 KB per SM), within 227 KB of shared memory.
+// TMA pipeline depth per CTA. Two 256-thread CTAs share an SM (each with its
+// own CTA barriers, so one computes while the other waits), so each CTA keeps
+// its ring within half of the SM's shared memory; the two rings together keep
+// enough boxes in flight to cover the DRAM latency (Little's law: ~64 KB per
+// SM). Measured on the three-continuum D-scheme at 1024^2: 500 ms per step
+// against 547 ms with one 512-thread CTA per SM and an 8-deep ring.
 __host__ __device__ constexpr int nstage(int L, bool coupled) {
-  return !coupled ? 8 : (L <= 1 ? 8 : (L == 2 ? 4 : (L == 3 ? 3 : 2)));
+  return !coupled ? 4 : (L <= 1 ? 4 : (L == 2 ? 2 : 1));
 }
 
 __device__ __forceinline__ double ldc(const double* p) { return __ldcg(p); }
@@ -1402,7 +1406,7 @@ __device__ __noinline__ bool scaled_finish(const StepParams& sp, unsigned mask, 
 // touched only at their own cells. Pass -1 runs with alpha = beta = 0 on
 // s = w = p = 0 and forms w_0 = A~ r_0 and the first inner products.
 __host__ __device__ constexpr int nstage1(int L, bool coupled) {
-  return !coupled ? 6 : (L <= 1 ? 6 : (L == 2 ? 3 : (L == 3 ? 2 : 1)));
+  return !coupled ? 3 : (L <= 1 ? 3 : 1);
 }
 
 template <int L, bool C>
