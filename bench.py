@@ -6,11 +6,13 @@ tau = 1/200, point sources +-1), synthetic and seeded. One benchmark step is
 one time step of the D-scheme: the fused exchange/right-hand-side pass and
 the three per-continuum PCG solves, one persistent kernel launch per step.
 
-Equal accuracy: every scheme is run at the PCG tolerance that keeps each step
-within rel-L2 1e-8 of its exact solve (measured on this workload over three
-steps against a 1e-13-tolerance run: D-scheme rtol 1e-10 -> 1.6e-10, coupled
-rtol 1e-11 -> 7.3e-9; the D-scheme value is also checked against the direct
-oracle by the full-size parity test).
+Equal accuracy: every scheme is run at the PCG tolerance that keeps it within
+rel-L2 1e-8 of its exact solve (measured on this workload over five steps
+from p^0 against a 1e-13-tolerance run: D-scheme rtol 1e-10 -> 7.5e-10,
+coupled rtol 1e-12 -> 1.5e-9 while 1e-11 leaves 1.7e-8; the D-scheme value is
+also checked against the direct oracle by the full-size parity test). The
+`equal_accuracy` line repeats that measurement on every run, for Jacobi and
+two-level PCG on both schemes, and reports time to solution at 1e-8.
 
 Metric: continuum-cell updates per second = L * nx * ny * steps / time. The
 FP64 step kernel is bound by the FP64 pipe on this GPU (2 FP64 FMA lanes per
@@ -63,7 +65,11 @@ METRIC = "continuum-cell updates/s (D-scheme at rel-L2 1e-8) and roofline fracti
 def workload_name(n):
     return ("triple_1024: 3 continua, %dx%d, tau=1/200, D-scheme FP64, rtol %g"
             % (n, n, RTOL_D))
-RTOL_COUPLED = 1e-11
+# The coupled system is worse conditioned: after 5 steps from p^0 the D-scheme at
+# rtol 1e-10 is within 7.5e-10 of its exact solve and the coupled scheme needs
+# rtol 1e-12 to come within 1.5e-9 (1e-11 leaves 1.7e-8): the equal-accuracy
+# line measures this on every run.
+RTOL_COUPLED = 1e-12
 RTOL_BATCH = 1e-12           # fracture continua: rtol 1e-10 leaves errors up to ~3e-8
 SMI_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -448,7 +454,7 @@ def support_means(fields, sup, nc):
     return np.concatenate(out)
 
 
-def equal_accuracy_extra(mc, w, torch, stream, opts_for, target=1e-9, nsteps=5):
+def equal_accuracy_extra(mc, w, torch, stream, opts_for, target=1e-8, nsteps=5):
     """Time to solution at equal accuracy on the headline workload: for the
     D-scheme and the coupled scheme, each with Jacobi and with the two-level
     preconditioner, `nsteps` steps from p^0 at rtol 1e-8 .. 1e-12. The

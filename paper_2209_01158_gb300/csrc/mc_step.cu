@@ -95,18 +95,34 @@ __device__ __forceinline__ void block_store(const double (&v)[NQ], unsigned qmas
   cta_reduce_store<NQ, NT, KMAX, double>(v, qmask, stage, partials, slot);
 }
 
+// Sum over b = lane, lane + 32, ... < nb of src[b], in that order. The first
+// PMAX loads are issued together (one L2 round trip for up to 32 * PMAX CTAs)
+// before the adds; the order of the adds, and so the result, is that of the
+// plain loop.
+constexpr int PMAX = 12;
+__device__ __forceinline__ double lane_partial_sum(const double* src, int lane, int nb) {
+  double v[PMAX];
+#pragma unroll
+  for (int j = 0; j < PMAX; ++j) v[j] = lane + 32 * j < nb ? ldc(src + lane + 32 * j) : 0.0;
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < PMAX; ++j)
+    if (lane + 32 * j < nb) s += v[j];
+  for (int b = lane + 32 * PMAX; b < nb; b += 32) s += ldc(src + b);
+  return s;
+}
+
 // Grid totals of NQ quantities into s_res (shared), readable by all threads.
+// Quantities whose bit is clear in qmask (stored as 0 by block_store) are not
+// summed: their totals are 0.
 template <int NQ>
-__device__ void grid_totals(const double* partials, int slot, double* s_res) {
+__device__ void grid_totals(const double* partials, int slot, double* s_res, unsigned qmask = ~0u) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   const int nb = gridDim.x;
   for (int k = warp; k < NQ; k += nw) {
-    const double* src = partials + ((size_t)slot * KMAX + k) * nb;
-    double s = 0.0;
-#pragma unroll 4
-    for (int b = lane; b < nb; b += 32) s += ldc(src + b);
-    s = warp_sum(s);
+    const double s =
+        (qmask >> k) & 1u ? warp_sum(lane_partial_sum(partials + ((size_t)slot * KMAX + k) * nb, lane, nb)) : 0.0;
     if (lane == 0) s_res[k] = s;
   }
   __syncthreads();
@@ -118,11 +134,7 @@ __device__ void grid_sum(const double* partials, int slot, double* s_res, double
   const int nw = blockDim.x >> 5;
   const int nb = gridDim.x;
   for (int k = warp; k < NQ; k += nw) {
-    const double* src = partials + ((size_t)slot * KMAX + k) * nb;
-    double s = 0.0;
-#pragma unroll 4
-    for (int b = lane; b < nb; b += 32) s += ldc(src + b);
-    s = warp_sum(s);
+    const double s = warp_sum(lane_partial_sum(partials + ((size_t)slot * KMAX + k) * nb, lane, nb));
     if (lane == 0) s_res[k] = s;
   }
   __syncthreads();
@@ -331,7 +343,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
   }
   block_store<3 * L>(acc, qbits(mask, L, 3), sm.box, sp.partials, 0);
   if (!grid_sync(sp)) return false;
-  grid_totals<3 * L>(sp.partials, 0, sm.res);
+  grid_totals<3 * L>(sp.partials, 0, sm.res, qbits(mask, L, 3));
   const double rtol2 = sp.rtol * sp.rtol;
   Scal64& S = *sm.sc;
   if (tid == 0) {
@@ -372,7 +384,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
     coarse_correct<L>(sp, active, sm, gc);
     block_store<L>(gc, active, sm.box, sp.partials, slot);
     if (!grid_sync(sp)) return false;
-    grid_totals<L>(sp.partials, slot, sm.res);
+    grid_totals<L>(sp.partials, slot, sm.res, active);
     slot ^= 1;
     if (tid == 0) {
       double gsum = 0.0;
@@ -565,7 +577,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
     }
     block_store<L>(pq, active, sm.box, sp.partials, slot);
     if (!grid_sync(sp)) { ok = false; break; }
-    grid_totals<L>(sp.partials, slot, sm.res);
+    grid_totals<L>(sp.partials, slot, sm.res, active);
     slot ^= 1;
     if (tid == 0) {
       double pqs = 0.0;
@@ -671,7 +683,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
     }
     block_store<2 * L>(acc2, qbits(active, L, 2), sm.box, sp.partials, slot);
     if (!grid_sync(sp)) { ok = false; break; }
-    grid_totals<2 * L>(sp.partials, slot, sm.res);
+    grid_totals<2 * L>(sp.partials, slot, sm.res, qbits(active, L, 2));
     slot ^= 1;
     ++it;
     if (tid == 0) {
@@ -709,7 +721,7 @@ __device__ bool pcg_solve(const StepParams& sp, const TmaMaps& maps, unsigned ma
       coarse_correct<L>(sp, active, sm, gc);
       block_store<L>(gc, active, sm.box, sp.partials, slot);
       if (!grid_sync(sp)) { ok = false; break; }
-      grid_totals<L>(sp.partials, slot, sm.res);
+      grid_totals<L>(sp.partials, slot, sm.res, active);
       slot ^= 1;
       if (tid == 0) {
         double gsum = 0.0;
@@ -932,7 +944,7 @@ __device__ __noinline__ bool scaled_init(const StepParams& sp, unsigned mask, Sm
   }
   block_store<3 * L>(acc, qbits(mask, L, 3), sm.box, sp.partials, 0);
   if (!grid_sync(sp)) return false;
-  grid_totals<3 * L>(sp.partials, 0, sm.res);
+  grid_totals<3 * L>(sp.partials, 0, sm.res, qbits(mask, L, 3));
   const double rtol2 = sp.rtol * sp.rtol;
   Scal64& S = *sm.sc;
   if (tid == 0) {
@@ -1142,7 +1154,7 @@ __device__ __noinline__ bool scaled_loop(const StepParams& sp, const TmaMaps& ma
     }
     block_store<L>(pq, active, sm.box, sp.partials, slot);
     if (!grid_sync(sp)) { ok = false; break; }
-    grid_totals<L>(sp.partials, slot, sm.res);
+    grid_totals<L>(sp.partials, slot, sm.res, active);
     slot ^= 1;
     if (tid == 0) {
       double pqs = 0.0;
@@ -1219,7 +1231,7 @@ __device__ __noinline__ bool scaled_loop(const StepParams& sp, const TmaMaps& ma
     const unsigned qm = chk ? qbits(active, L, 2) : (active << L);
     block_store<2 * L>(acc2, qm, sm.box, sp.partials, slot);
     if (!grid_sync(sp)) { ok = false; break; }
-    grid_totals<2 * L>(sp.partials, slot, sm.res);
+    grid_totals<2 * L>(sp.partials, slot, sm.res, qm);
     slot ^= 1;
     ++it;
     if (tid == 0) {
@@ -1612,7 +1624,7 @@ __device__ __noinline__ bool sp1_loop(const StepParams& sp, const TmaMaps& maps,
     const unsigned qm = chk ? qbits(active, L, 3) : qbits(active, L, 2);
     block_store<3 * L>(dots, qm, sm.box, sp.partials, slot);
     if (!grid_sync(sp)) { ok = false; break; }
-    grid_totals<3 * L>(sp.partials, slot, sm.res);
+    grid_totals<3 * L>(sp.partials, slot, sm.res, qm);
     slot ^= 1;
     if (tid == 0) {
       double sg = 0.0, sd = 0.0, sr = 0.0;
