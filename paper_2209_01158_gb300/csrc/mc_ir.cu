@@ -54,11 +54,64 @@ constexpr int NBOX = 4;                 // box slots per ring stage (3 used by t
 constexpr int KM = MC_KMAX_ALLOC;
 
 __device__ __forceinline__ float tload(const float* p, long long i) { return __ldg(p + i); }
-// BF16 transmissibilities through the read-only path: the 16-bit pattern is
-// loaded with ld.global.nc and widened to FP32 (exact).
-__device__ __forceinline__ float tload(const __nv_bfloat16* p, long long i) {
-  const unsigned short bits = __ldg(reinterpret_cast<const unsigned short*>(p) + i);
-  return __uint_as_float((unsigned)bits << 16);
+
+// The face transmissibilities of this lane's cell (gx, gy): east te = TE[i],
+// west tw = TE[i - 1], north tn = TN[i], south ts = TN[i - pitch] (0 where
+// the face does not exist). All 32 lanes of the warp call it, for the 32
+// consecutive cells gx = x0w + lane of one row (x0w a multiple of 32); cells
+// outside the grid get 0 and load nothing.
+__device__ __forceinline__ void tfaces(const float* TE, const float* TN, long long i, int gx, int gy, int nx,
+                                       int ny, int pitch, float& te, float& tw, float& tn, float& ts) {
+  te = tw = tn = ts = 0.f;
+  if (gx < nx && gy < ny) {
+    te = tload(TE, i);
+    tn = tload(TN, i);
+    if (gx > 0) tw = tload(TE, i - 1);
+    if (gy > 0) ts = tload(TN, i - pitch);
+  }
+}
+
+// BF16: the row's values are read as 32-bit words (two BF16 each, rows start
+// on 32-byte boundaries since the pitch is a multiple of 16) and handed out by
+// warp shuffles. TE: lanes 0..16 read the 17 words covering columns
+// x0w - 2 .. x0w + 31, which hold every lane's east and west face. TN: lanes
+// 0..15 read the 16 words of row gy, lanes 16..31 those of row gy - 1. Two
+// loads per row instead of four; a word that lies outside the grid's rows or
+// the array is not read (0). The values are exactly those of the scalar loads.
+__device__ __forceinline__ float bf16_half(unsigned w, int hi) {
+  return __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
+}
+__device__ __forceinline__ void tfaces(const __nv_bfloat16* TE, const __nv_bfloat16* TN, long long i, int gx,
+                                       int gy, int nx, int ny, int pitch, float& te, float& tw, float& tn,
+                                       float& ts) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int x0w = gx - lane;
+  const long long row = i - gx;  // gy * pitch
+  const unsigned* E = reinterpret_cast<const unsigned*>(TE);
+  const unsigned* Nn = reinterpret_cast<const unsigned*>(TN);
+  unsigned we = 0u, wn = 0u;
+  {
+    const int c = x0w - 2 + 2 * lane;  // first column of this lane's TE word
+    if (lane <= 16 && gy < ny && c >= 0 && c + 1 < pitch) we = __ldg(E + ((row + c) >> 1));
+  }
+  {
+    const int k = lane & 15;
+    const int c = x0w + 2 * k;
+    const int r = lane < 16 ? gy : gy - 1;
+    if (r >= 0 && r < ny && c + 1 < pitch) wn = __ldg(Nn + (((long long)r * pitch + c) >> 1));
+  }
+  const unsigned e1 = __shfl_sync(full, we, (lane + 2) >> 1);
+  const unsigned e0 = __shfl_sync(full, we, (lane + 1) >> 1);
+  const unsigned n1 = __shfl_sync(full, wn, lane >> 1);
+  const unsigned n0 = __shfl_sync(full, wn, 16 + (lane >> 1));
+  te = tw = tn = ts = 0.f;
+  if (gx < nx && gy < ny) {
+    te = bf16_half(e1, lane & 1);
+    tn = bf16_half(n1, lane & 1);
+    if (gx > 0) tw = bf16_half(e0, (lane + 1) & 1);
+    if (gy > 0) ts = bf16_half(n0, lane & 1);
+  }
 }
 
 // The CTAs that cooperate on one solve: the whole grid, or one team of the
@@ -276,12 +329,9 @@ __device__ bool inner_single(const IrParams& ip, const TmaMaps& maps, unsigned a
       for (int j = 0; j < CPT; ++j) {
         const int gy = y0 + ly + RPT * j;
         const long long i = (long long)gy * pitch + gx;
-        te[j] = tw[j] = tn[j] = ts[j] = dc[j] = pold[j] = dold[j] = 0.f;
+        tfaces(TE, TN, i, gx, gy, nx, ny, pitch, te[j], tw[j], tn[j], ts[j]);
+        dc[j] = pold[j] = dold[j] = 0.f;
         if (gx < nx && gy < ny) {
-          te[j] = tload(TE, i);
-          tn[j] = tload(TN, i);
-          if (gx > 0) tw[j] = tload(TE, i - 1);
-          if (gy > 0) ts[j] = tload(TN, i - pitch);
           dc[j] = ip.dc32[a0] ? __ldg(ip.dc32[a0] + i) : ip.dcf[a0];
           pold[j] = __ldcg(ip.p32[a0] + i);
           dold[j] = __ldcg(ip.d32[a0] + i);
@@ -659,12 +709,9 @@ __device__ bool ir_solve(const IrParams& ip, const TmaMaps& maps, unsigned mask,
         for (int j = 0; j < CPT; ++j) {
           const int gy = y0 + ly + RPT * j;
           const long long i = (long long)gy * pitch + gx;
-          te[j] = tw[j] = tn[j] = ts[j] = dc[j] = 0.f;
+          tfaces(TE, TN, i, gx, gy, nx, ny, pitch, te[j], tw[j], tn[j], ts[j]);
+          dc[j] = 0.f;
           if (gx < nx && gy < ny) {
-            te[j] = tload(TE, i);
-            tn[j] = tload(TN, i);
-            if (gx > 0) tw[j] = tload(TE, i - 1);
-            if (gy > 0) ts[j] = tload(TN, i - pitch);
             dc[j] = ip.dc32[a0] ? __ldg(ip.dc32[a0] + i) : ip.dcf[a0];
           }
         }
