@@ -44,3 +44,19 @@ def test_traffic_single_source_record(tmp_path, monkeypatch):
     _tree(tmp_path, {"k.cu": "kernel"}, rec)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_per_unit("k") == 18.0
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` runs the CPU oracle on a crop and prints one
+    JSON line with the reference arm's keys (no GPU needed)."""
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0", "--crop", "32"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    for k in ("metric", "unit", "higher_is_better", "config", "cpu_baseline", "e2e"):
+        assert k in line
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
