@@ -81,3 +81,21 @@ def test_host_only_calls(lib):
                         ctypes.byref(out)) == mc.N.MC_E_ARG
     assert b"grid" in lib.mc_last_error(None)
     assert lib.mc_step_decoupled(None, 0, 1, None) == mc.N.MC_E_ARG
+
+
+def test_binding_constants_match_the_header():
+    """Every integer constant the header defines (#define or enumerator) has
+    the same value in the Python binding."""
+    from paper_2209_01158_gb300 import _native
+    vals = {}
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^\s*#define\s+(MC_[A-Z0-9_]+)\s+(-?\d+)\s*$", text, re.M):
+            vals[m.group(1)] = int(m.group(2))
+        for m in re.finditer(r"\b(MC_[A-Z0-9_]+)\s*=\s*(-?\d+)", text):
+            vals[m.group(1)] = int(m.group(2))
+    assert len(vals) >= 20, vals
+    missing = [k for k in vals if not hasattr(_native, k)]
+    assert not missing, missing
+    wrong = {k: (v, getattr(_native, k)) for k, v in vals.items() if getattr(_native, k) != v}
+    assert not wrong, wrong
